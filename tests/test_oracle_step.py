@@ -1,0 +1,204 @@
+"""Pins of the oracle's time step (Eq. (rlb:disc), Sec. II.D, Sec. III)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import projection as pj
+from paper_inputs import fields as gen
+
+PAPER = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+HBARC = 0.1973269804  # GeV fm (CODATA)
+
+
+def near_equilibrium(lat, shape, seed, amp=0.02, vmax=0.3):
+    """Equilibrium of smooth random fields plus a small random non-equilibrium part."""
+    n, T, u = gen.smooth_random_fields(shape, seed=seed, vmax=vmax, sigma_lnT=0.1)
+    o = oracle.OracleRLB(lat, shape[2], shape[1], shape[0])
+    o.init(n, T, u)
+    rng = np.random.default_rng(seed + 1000)
+    scale = lat.w[:, None, None, None] * n[None] / 2
+    return o.f + amp * scale * rng.standard_normal(o.f.shape)
+
+
+def pull(lat, f, bc):
+    nz, ny, nx = f.shape[1:]
+    out = np.empty_like(f)
+    for i, (vx, vy, vz) in enumerate(lat.v):
+        idx = []
+        for ax, (nn, vv) in enumerate(((nz, vz), (ny, vy), (nx, vx))):
+            src = np.arange(nn) - vv
+            b = bc[2 - ax]
+            idx.append(np.mod(src, nn) if b == 0 else np.clip(src, 0, nn - 1))
+        out[i] = f[i][np.ix_(*idx)]
+    return out
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0), (0, 1, 1)])
+def test_streaming_moves_population_i_by_v_i(lat3, bc):
+    """Eq. (rlb:disc) left-hand side: f_i(x + v_i, t + 1) is built from f_i(x, t).  With a relaxation
+    time of 1e15 the collision changes nothing above 1e-15, so one step is a pure shift."""
+    shape = (5, 4, 7)
+    f = near_equilibrium(lat3, shape, seed=1)
+    o = oracle.OracleRLB(lat3, shape[2], shape[1], shape[0], bc=bc, tau_prime=1e15)
+    o.set_populations(f)
+    o.step(1)
+    scale = lat3.w[:, None, None, None]  # populations are O(w_i n / 2) with n ~ 1
+    assert np.max(np.abs(o.f - pull(lat3, f, bc)) / scale) < 1e-13
+
+
+@pytest.mark.parametrize("order", [3, 2])
+@pytest.mark.parametrize("u", [(0.0, 0.0, 0.0), (0.3, -0.2, 0.4)])
+def test_uniform_state_is_stationary(order, u):
+    """A uniform equilibrium streams onto itself and is a fixed point of the collision."""
+    lat = oracle.read_lattice(order)
+    o = oracle.OracleRLB(lat, 3, 2, 4, bc=(0, 0, 1), eta_over_s=0.1)
+    o.init(0.8, 1.2, np.array(u)[:, None, None, None])
+    f0 = o.f.copy()
+    o.step(200)
+    # Round-off only: populations move by < 1e-13 of their scale per step, the fields not at all.
+    scale = np.maximum(np.abs(f0), lat.w[:, None, None, None] * 0.8 / 2)
+    assert np.max(np.abs(o.f - f0) / scale) < 200 * 1e-13
+    n, eps, U, _ = o.moments()
+    assert np.allclose(n, 0.8, rtol=1e-12) and np.allclose(eps, 3 * 0.8 * 1.2, rtol=1e-12)
+    g = 1 / np.sqrt(1 - np.dot(u, u))
+    assert np.allclose(U.reshape(4, -1).T, g * np.r_[1.0, u], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("order", [3, 2])
+def test_conservation_periodic(order):
+    """Eqs. (eq:conser1), (eq:conser2): under periodic boundaries sum_x N^0 and sum_x T^{0 nu} are
+    invariant (the collision conserves them cell by cell through Landau matching)."""
+    lat = oracle.read_lattice(order)
+    shape = (4, 5, 6)
+    o = oracle.OracleRLB(lat, shape[2], shape[1], shape[0], eta_over_s=0.1)
+    o.set_populations(near_equilibrium(lat, shape, seed=4, amp=0.05, vmax=0.5))
+    t0 = o.moments()[3]
+    o.step(30)
+    t1 = o.moments()[3]
+    assert o.nonconv == 0
+    assert np.max(np.abs(t1 - t0)) < 1e-13 * np.max(np.abs(t0))
+
+
+def numpy_step(lat, f, bc, tau):
+    """One step written independently with numpy: np indexing for the pull, einsum moments, a dense
+    eigen-solver for Landau matching, the Gram-Schmidt projection for f^eq."""
+    ft = pull(lat, f, bc)
+    p = lat.momenta()
+    eta = np.diag([1.0, -1, -1, -1])
+    out = np.empty_like(f)
+    for z, y, x in np.ndindex(*f.shape[1:]):
+        fc = ft[:, z, y, x]
+        N = fc @ p
+        Tm = np.einsum("i,ia,ib->ab", fc, p, p)
+        vals, vecs = np.linalg.eig(Tm @ eta)
+        k = [j for j in range(4) if abs(vals[j].imag) == 0 and np.real(vecs[:, j]) @ eta @ np.real(vecs[:, j]) > 0][0]
+        U = np.real(vecs[:, k])
+        U = U / math.sqrt(U @ eta @ U)
+        U = U if U[0] > 0 else -U
+        eps = float(np.real(vals[k]))
+        n = float(U @ eta @ N)
+        T = eps / (3 * n)
+        feq = pj.equilibrium(lat, n, T, U)
+        om = (p @ eta @ U) / (lat.p0 * tau(T))
+        out[:, z, y, x] = fc - om * (fc - feq)
+    return out
+
+
+@pytest.mark.parametrize("order", [3, 2])
+@pytest.mark.parametrize("bc", [(0, 0, 0), (1, 0, 1)])
+def test_step_matches_independent_numpy_step(order, bc):
+    lat = oracle.read_lattice(order)
+    shape = (3, 2, 4)
+    f = near_equilibrium(lat, shape, seed=7 + order, amp=0.05, vmax=0.5)
+    eta_s = 0.1
+    kappa = 0.4 * 0.008 / HBARC
+    tau = lambda T: 0.5 + 6 * eta_s / (lat.R * kappa * T)
+    o = oracle.OracleRLB(lat, shape[2], shape[1], shape[0], bc=bc, eta_over_s=eta_s)
+    o.set_populations(f)
+    o.step(1)
+    ref = numpy_step(lat, f, bc, tau)
+    scale = lat.w[:, None, None, None] * np.max(np.abs(f / lat.w[:, None, None, None]))
+    assert np.max(np.abs(o.f - ref) / scale) < 1e-11
+
+
+def test_tau_prime_from_eta_over_s():
+    """eta = (2/3) P tau (Sec. II.D) with s = 4 n (Sec. III) gives a physical relaxation time
+    tau = 6 (eta/s) hbar / T; one lattice step is the printed dt = sqrt(41) * 0.008 fm/c (Sec. III);
+    the lattice correction adds one half step.  At eta/s = 0.5 and T = 400 MeV this is tau' ~ 29,
+    inside the paper's 20-40 (Sec. III)."""
+    dt = PAPER["time_step_fm"]["third_order"]
+    assert dt == pytest.approx(math.sqrt(41) * 0.008)
+    for eta_s in (0.01, 0.1, 0.5):
+        tau_phys = 6 * eta_s * HBARC / 0.4  # fm/c
+        assert oracle.tau_prime(eta_s, math.sqrt(41), 1.0) == pytest.approx(0.5 + tau_phys / dt, rel=1e-12)
+    assert 20 <= oracle.tau_prime(0.5, math.sqrt(41), 1.0) <= 40
+    # second order: dt = 3 * 0.008 fm/c
+    assert oracle.tau_prime(0.1, 3.0, 1.0) == pytest.approx(0.5 + 6 * 0.1 * HBARC / 0.4 / PAPER["time_step_fm"]["second_order"])
+
+
+def shear_decay_rate(lat, nx, tau, steps=300, skip=40, amp=1e-4):
+    x = np.arange(nx)
+    uy = amp * np.sin(2 * np.pi * x / nx)
+    o = oracle.OracleRLB(lat, nx, 1, 1, tau_prime=tau)
+    o.init(1.0, 1.0, np.stack([np.zeros(nx), uy, np.zeros(nx)])[:, None, None, :])
+    ts, amps = [], []
+    for t in range(steps + 1):
+        if t >= skip and t % 10 == 0:
+            U = o.moments()[2]
+            mode = np.fft.rfft(U[2, 0, 0, :])[1]
+            ts.append(t)
+            amps.append(abs(mode))
+        if t < steps:
+            o.step(1)
+    return -np.polyfit(ts, np.log(amps), 1)[0]
+
+
+@pytest.mark.slow
+def test_shear_wave_decay_rate(lat3):
+    """Transverse momentum diffuses with rate eta k^2 / (eps + P) = eta k^2 / (4P).  With the lattice
+    correction (tau' - 1/2) and one step = R light-crossing times, the rate per step is
+    c_eta R^2 (tau' - 1/2) k^2 / 4 where eta = c_eta P R (tau' - 1/2).  The scheme's rate scales as
+    k^2 and as (tau' - 1/2); its coefficient is that of the Chapman-Enskog solution of the
+    Anderson-Witting equation for a massless gas, c_eta = 4/5 (the paper prints 2/3, Sec. II.D)."""
+    R2 = lat3.R2
+    rates = {}
+    for nx, tau in ((128, 0.6), (128, 0.7), (96, 0.6)):
+        g = shear_decay_rate(lat3, nx, tau)
+        k = 2 * np.pi / nx
+        rates[(nx, tau)] = g / (R2 * (tau - 0.5) * k * k / 4)
+    c = np.array(list(rates.values()))
+    assert np.all(np.abs(c - 0.8) < 0.02), rates
+    assert np.ptp(c) < 0.01, rates
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("order", [3, 2])
+def test_riemann_tube_runs(order):
+    """Sec. III shock tube on 1x1x800 with copy-out ends: initial pressures 1.0 | 0.0625 (printed
+    0.062), flow from the hot to the cold side, no Landau failure over 500 steps.  While the ends are
+    undisturbed (waves move at most R cells per step), particle number and energy are conserved and
+    the total z-momentum grows by the pressure impulse (P_left - P_right) t, with t = R per step in
+    units of dx / c (time dilatation, Sec. II.C)."""
+    lat = oracle.read_lattice(order)
+    g = PAPER["riemann_initial_state"]
+    n, T, u = gen.riemann_tube(g["nz"], g["T_left"], g["T_right"])
+    assert n[0, 0, 0] * T[0, 0, 0] == pytest.approx(g["P_left"])
+    assert abs(n[-1, 0, 0] * T[-1, 0, 0] - g["P_right_printed"]) < g["P_right_abs_tol"]
+    o = oracle.OracleRLB(lat, 1, 1, g["nz"], bc=(0, 0, 1), eta_over_s=0.1)
+    o.init(n, T, u)
+    t0 = o.moments()[3]
+    o.step(60)
+    nn, eps, U, t1 = o.moments()
+    vz = U[3, :, 0, 0] / U[0, :, 0, 0]
+    assert o.nonconv == 0
+    assert 0.2 < vz.max() < 0.8 and vz.min() > -1e-3
+    assert np.allclose(t1[:2], t0[:2], rtol=1e-12, atol=0)
+    assert np.allclose(t1[2:4], 0.0, atol=1e-12 * t0[1])
+    impulse = (g["P_left"] - n[-1, 0, 0] * T[-1, 0, 0]) * 60 * lat.R
+    assert t1[4] == pytest.approx(impulse, rel=1e-10)
+    o.step(440)
+    assert o.nonconv == 0 and np.all(np.isfinite(o.f))
