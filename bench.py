@@ -1,0 +1,300 @@
+"""Throughput benchmark of the relativistic lattice Boltzmann step on GB300.
+
+Workload (one "step" = one time step of the whole lattice through the fused pull-collide kernel):
+the 256^3 periodic random-field case of the third-order model (Q = 128) with float storage:
+velocity from Fourier modes |k| <= 4 rescaled to max |v| = 0.6, log-normal temperature
+(sigma 0.2, mean 1), n = T^3, eta/s = 0.1 with the local-temperature relaxation time.
+
+Prints one JSON line:
+  value      MLUPS (million lattice-cell updates per second) with the state resident in HBM;
+  e2e        the same metric for a whole job through the C ABI from pinned host buffers
+             (rlb_init from host fields, K steps, rlb_moments back to host);
+  roofline   the step kernel's algorithmic bytes (Q x 2 x 4 bytes per cell update) per launch over
+             its CUDA-event duration, against the measured HBM copy bandwidth;
+  cpu_baseline  the FP64 oracle on the host cores, on a bounded sample of the same workload;
+  fp64_plain the same lattice with double storage and arithmetic (MLUPS).
+
+--impl reference times the oracle alone (the reference arm of this comparison).
+Multi-GPU (torchrun): every rank steps its own independent lattice (replicas; no collective on the
+data path); value = all ranks' cell updates / the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_inputs import fields as gen  # noqa: E402
+
+METRIC = "MLUPS"
+BASELINE_METRIC = "MLUPS & HBM-roofline %, FP32 batched vs FP64 plain at <=1e-5 rel err; p50/p99"
+N_LATTICE = 256
+ORDER = 3
+Q = 128
+ETA_S = 0.1
+WORKLOAD = "random-field 256^3 periodic, third-order RLB (Q=128, R^2=41), FP32 storage, eta/s=0.1"
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def cpu_baseline(budget_s=12.0):
+    """The FP64 oracle, as it stands, on one host core: 32^3 periodic lattice of the same
+    random-field generator, stepping until about budget_s seconds are spent."""
+    import oracle
+    lat = oracle.read_lattice(ORDER)
+    n_side = 32
+    n, T, u = gen.smooth_random_fields((n_side,) * 3, seed=1, vmax=0.6, sigma_lnT=0.2)
+    o = oracle.OracleRLB(lat, n_side, n_side, n_side, eta_over_s=ETA_S)
+    o.init(n, T, u)
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < budget_s:
+        o.step(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": n_side ** 3 * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "%d steps of a %d^3 periodic lattice of the same random-field workload (serial FP64 C "
+                      "oracle, %.1f s)" % (steps, n_side, n_side, dt)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    cb = cpu_baseline(budget_s=max(3.0, 4.0 * args.steps / max(args.steps, 1)))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("FP32 storage", "FP64 CPU oracle"), "sample": cb["sample"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=N_LATTICE, help="lattice edge (default 256)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+
+    from paper_1301_3423_gb300 import RLB
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    N = args.n
+    shape = (N, N, N)
+    cells = N ** 3
+    n, T, u = gen.smooth_random_fields(shape, seed=1 + rank, vmax=0.6, sigma_lnT=0.2)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- device-resident throughput (the headline value) ------------------------------------
+    g = RLB(shape, order=ORDER, storage="f32", eta_over_s=ETA_S, stream=stream)
+    g.init(n, T, u)
+    g.step(args.warmup)
+    g.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = g.kernel_launches
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t_wall = time.perf_counter()
+        e0.record(stream)
+        g.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    torch.cuda.synchronize()
+    barrier()
+    launches = g.kernel_launches - launches0
+    ms_total = e0.elapsed_time(e1)
+    ms_total_max = max_over_ranks(ms_total)
+    g.sync()
+    value = world * cells * args.steps / (ms_total_max * 1e-3) / 1e6
+    per_launch_s = ms_total * 1e-3 / launches
+    algo_bytes = cells * Q * 2 * 4
+    peaks, peak_src = measured_peaks()
+    achieved = algo_bytes / per_launch_s / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "step_f32_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            traffic = json.load(open(tpath)).get("bytes_per_launch_256")
+        except (OSError, ValueError):
+            traffic = None
+    g.close()
+
+    # ---- FP64 plain path on the same lattice ------------------------------------------------
+    fp64 = None
+    if not args.no_fp64:
+        k64 = max(3, args.steps // 30)
+        g64 = RLB(shape, order=ORDER, storage="f64", eta_over_s=ETA_S, stream=stream)
+        g64.init(n, T, u)
+        g64.step(2)
+        g64.sync()
+        e0.record(stream)
+        g64.step(k64)
+        e1.record(stream)
+        e1.synchronize()
+        ms64 = max_over_ranks(e0.elapsed_time(e1))
+        g64.sync()
+        g64.close()
+        fp64 = {"value": world * cells * k64 / (ms64 * 1e-3) / 1e6, "unit": "MLUPS", "steps": k64,
+                "ms_per_step": ms64 / k64, "bound": "fp64 alu"}
+
+    # ---- end to end through the C ABI from pinned host buffers -------------------------------
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        hn, hT, hu = pin(n), pin(T), pin(u)
+        on, oe, oU = (torch.empty(shape, dtype=torch.float64).pin_memory(),
+                      torch.empty(shape, dtype=torch.float64).pin_memory(),
+                      torch.empty((4,) + shape, dtype=torch.float64).pin_memory())
+        ge = RLB(shape, order=ORDER, storage="f32", eta_over_s=ETA_S, stream=stream)
+        ptr = lambda t: t.numpy()
+        ge.init(ptr(hn), ptr(hT), ptr(hu))
+        ge.step(args.warmup)
+        ge.sync()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ge.init(ptr(hn), ptr(hT), ptr(hu))
+        ge.step(args.steps)
+        ge.moments(out=dict(n=on.numpy(), eps=oe.numpy(), U=oU.numpy()))
+        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        ge.close()
+        h2d = 5 * cells * 8
+        d2h = 6 * cells * 8 + 5 * 8
+        e2e = {"value": world * cells * args.steps / t_e2e / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "job": "rlb_init from pinned host fields + %d steps + rlb_moments to host" % args.steps}
+
+    if rank != 0:
+        return
+    cb = None if args.no_cpu_baseline else cpu_baseline()
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_total_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": [N, N, N], "order": ORDER, "q": Q, "storage": "f32",
+                   "eta_over_s": ETA_S, "boundary": "periodic", "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2: two population buffers of %.1f GB" % (cells * Q * 4 / 1e9),
+                   "baseline_metric": BASELINE_METRIC},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                     "peak_source": peak_src, "algorithmic_bytes_per_launch": algo_bytes,
+                     "kernel": "k_step<Quad3, StoreF32>", "launch_ms": per_launch_s * 1e3},
+        "cpu_baseline": cb,
+        "e2e": e2e,
+        "fp64_plain": fp64,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "wall_s_timed_region": t_wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,160 @@
+/*
+ * rlb.h -- C ABI of librlb, the GB300 (sm_103a) implementation of the relativistic lattice
+ * Boltzmann model with improved dissipation (Mendoza, Karlin, Succi, Herrmann, arXiv:1301.3423).
+ *
+ * The model (Sec. II):
+ *   - one population f_i per discrete 4-momentum p_i^mu = p0_i (1, v_i / R), v_i integer with
+ *     |v_i|^2 = R^2 (Eqs. (eq:dio), (eq:mrecon2)); third order: R^2 = 41, Q = 128 (Sec. II.C);
+ *     second order: R^2 = 9, Q = 66 (App. A);
+ *   - one time step of the time-dilated equation (Eq. (rlb:disc), delta x = delta t' = 1):
+ *       f_i(x + v_i, t' + 1) = f_i(x, t') - (p_i^mu U_mu) / (tau' p0_i) (f_i - f_i^eq),
+ *     with U^mu, eps, n from Landau matching T^{ab} U_b = eps U^a, n = U_mu N^mu, eps = 3 n T
+ *     (Eq. (eigenproblem), Sec. II.D) and f_i^eq the projected Maxwell-Juttner equilibrium
+ *     (Eq. (eq:disc1); explicit forms Eq. (eq:equi3rd), Eq. (eq:equi2nd)).
+ *
+ * Lattice and memory.  Cells are indexed (x, y, z) with x fastest: cell = (z * ny + y) * nx + x.
+ * Field arrays passed to this ABI are double precision, structure of arrays: a scalar field is
+ * double[cells], a vector field is double[components][cells].  Populations are
+ * double[q][cells] at the boundary, whatever the storage precision inside.
+ *
+ * Conventions common to every call.
+ *   - Every call returns an rlb_status and never aborts, traps or throws.
+ *   - Work is enqueued on the context's CUDA stream; rlb_step returns before the GPU finishes.
+ *     Kernel faults and per-cell failures (Landau matching without a timelike solution) are
+ *     reported by the next synchronising call (rlb_sync, rlb_moments, rlb_get_populations).
+ *   - The caller owns every buffer it passes; the library copies what it needs before returning
+ *     (host buffers) or before the enqueued work completes (device buffers: keep them alive and
+ *     unmodified until the next synchronising call).
+ *   - A context is used by one host thread at a time.
+ *   - rlb_last_error() describes the most recent failure of that context.
+ */
+#ifndef RLB_H
+#define RLB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rlb_ctx rlb_ctx;
+
+typedef enum {
+  RLB_OK = 0,
+  RLB_EINVAL = 1,   /* invalid argument or parameter (nothing was changed) */
+  RLB_ENOMEM = 2,   /* device memory could not be allocated */
+  RLB_ECUDA = 3,    /* a CUDA call failed; the context should be destroyed */
+  RLB_ENONCONV = 4, /* Landau matching found no timelike eigenvector in some cell */
+  RLB_ENAN = 5,     /* non-finite populations were produced */
+  RLB_ETIMEOUT = 6, /* a bounded device-side wait expired */
+  RLB_ESTATE = 7    /* call not valid in the context's current state */
+} rlb_status;
+
+typedef enum { RLB_BC_PERIODIC = 0, RLB_BC_COPYOUT = 1 } rlb_bc;
+
+/* Storage precision of the populations in device memory.
+ *   RLB_F64   : double populations, double arithmetic.
+ *   RLB_F32   : float populations, float arithmetic; Landau matching in double above gamma_thr.
+ *   RLB_F16DEV: half-precision store of d_i = f_i / w_i - n_ref / 2 (the deviation from the
+ *               weight-scaled rest equilibrium at density n_ref, temperature 1), float arithmetic. */
+typedef enum { RLB_F64 = 0, RLB_F32 = 1, RLB_F16DEV = 2 } rlb_storage;
+
+typedef struct {
+  int order;          /* 3: third-order model, R^2 = 41, Q = 128 (Sec. II.C); 2: second order,
+                         R^2 = 9, Q = 66 (App. A) */
+  int nx, ny, nz;     /* lattice size in cells, each >= 1 */
+  int bc[3];          /* per axis x, y, z: RLB_BC_PERIODIC, or RLB_BC_COPYOUT (a population pulled
+                         from outside the lattice is taken from the nearest edge cell) */
+  double eta_over_s;  /* shear viscosity over entropy density; mapped to tau' by
+                         tau' = 1/2 + 6 (eta/s) / (R kappa T), kappa = T_unit_GeV dx_fm / (hbar c)
+                         (Sec. II.D, Sec. III), unless tau_prime > 1/2 */
+  double tau_prime;   /* > 1/2: constant relaxation time in lattice units; otherwise mapped */
+  int tau_local_T;    /* 1: T in the mapping is each cell's Landau temperature; 0: T_ref */
+  double T_ref;       /* reference temperature in lattice units (default 1.0 = 400 MeV, Sec. III) */
+  double dx_fm;       /* cell size in fm (default 0.008, Sec. III) */
+  double T_unit_GeV;  /* lattice temperature unit in GeV (default 0.4, Sec. III) */
+  int storage;        /* rlb_storage */
+  int landau_fp64;    /* RLB_F32 / RLB_F16DEV only: 1 = always solve Landau matching in double */
+  double gamma_thr;   /* RLB_F32 / RLB_F16DEV only: cells whose Eckart Lorentz factor exceeds this
+                         are solved in double (default 2.0) */
+  double n_ref;       /* RLB_F16DEV only: reference density of the stored deviation (default 1.0) */
+  void* stream;       /* cudaStream_t to enqueue on; NULL = the default stream */
+  /* Optional quadrature (Sec. II.C, App. A).  When q > 0 these arrays are compared with the
+   * quadrature compiled into the library for this order and must match exactly (RLB_EINVAL
+   * otherwise); rlb_quadrature() returns the built-in one. */
+  int q;
+  const int* vel;     /* [q][3] integer velocities v_i */
+  const int* level;   /* [q] energy level of each population */
+  const double* p0;   /* [q] energy p0_i */
+  const double* w;    /* [q] weight w_i */
+} rlb_params;
+
+/* Fill *p with the defaults above: order 3, 1x1x1 periodic, eta/s 0.1 mapped with the local
+ * temperature, T_ref 1, dx 0.008 fm, T unit 0.4 GeV, RLB_F64 storage, gamma_thr 2, n_ref 1, default
+ * stream, no quadrature check. */
+void rlb_default_params(rlb_params* p);
+
+/* Device bytes a context with these parameters allocates (two population buffers plus fields
+ * and reduction scratch).  0 if the parameters are invalid. */
+size_t rlb_bytes_required(const rlb_params* p);
+
+/* Create a context: validate parameters, allocate two population buffers of q * cells elements
+ * in the storage precision and the per-cell field and reduction buffers on the current device.
+ * *out receives the handle (NULL on failure).  Errors: RLB_EINVAL, RLB_ENOMEM, RLB_ECUDA. */
+rlb_status rlb_create(const rlb_params* p, rlb_ctx** out);
+
+/* Set every population to the discrete equilibrium f_i^eq(n, T, U) (Eq. (eq:disc1)) of the given
+ * fields, U = gamma (1, u): n, T double[cells], u double[3][cells] (u_x, u_y, u_z, |u| < 1).
+ * on_device = 0: host pointers (copied before return); 1: device pointers.  Resets the step
+ * counter to 0.  Errors: RLB_EINVAL (null pointer; invalid values are reported as RLB_EINVAL by
+ * the next synchronising call), RLB_ECUDA. */
+rlb_status rlb_init(rlb_ctx* ctx, const double* n, const double* T, const double* u, int on_device);
+
+/* Enqueue nsteps >= 0 time steps of Eq. (rlb:disc): pull streaming by v_i, then Anderson-Witting
+ * collision with Landau matching in every cell.  Asynchronous.  Errors: RLB_EINVAL, RLB_ECUDA. */
+rlb_status rlb_step(rlb_ctx* ctx, long nsteps);
+
+/* Landau-frame fields of the pre-collision populations of the current time level (the initial
+ * populations before the first step; afterwards the populations the last step pulled): n, eps
+ * double[cells], U double[4][cells] (U^0..U^3), and totals[5] = sum over cells of N^0, T^00,
+ * T^0x, T^0y, T^0z (the conserved densities of Eqs. (eq:conser1), (eq:conser2)), summed in double
+ * in a fixed order.  Any output pointer may be NULL.  on_device = 1: n, eps, U are device
+ * pointers (totals is always host).  Synchronises the stream.  Errors: RLB_ENONCONV (cells without
+ * a Landau frame; their fields are NaN), RLB_ENAN, RLB_ECUDA. */
+rlb_status rlb_moments(rlb_ctx* ctx, double* n, double* eps, double* U, double totals[5], int on_device);
+
+/* Wait for enqueued work and report deferred errors (as rlb_moments). */
+rlb_status rlb_sync(rlb_ctx* ctx);
+
+/* Copy the stored (post-collision) populations out as double[q][cells].  Synchronises. */
+rlb_status rlb_get_populations(rlb_ctx* ctx, double* f, int on_device);
+
+/* Replace the stored populations by double[q][cells] values (converted to the storage precision)
+ * and treat them as the initial state: the step counter is reset to 0 and rlb_moments reports
+ * their own fields.  Errors: RLB_EINVAL, RLB_ECUDA. */
+rlb_status rlb_set_populations(rlb_ctx* ctx, const double* f, int on_device);
+
+/* Number of time steps taken since rlb_init / rlb_set_populations (-1 for NULL). */
+long rlb_steps_done(const rlb_ctx* ctx);
+
+/* Kernel launches this context has enqueued since creation (-1 for NULL). */
+long rlb_kernel_launches(const rlb_ctx* ctx);
+
+/* Release the context's device memory.  NULL is accepted.  Synchronises the stream. */
+rlb_status rlb_destroy(rlb_ctx* ctx);
+
+/* Text of the context's most recent error ("" if none).  Valid until the next call on ctx.
+ * With ctx == NULL: the most recent rlb_create failure of the calling thread. */
+const char* rlb_last_error(const rlb_ctx* ctx);
+
+/* The quadrature built into the library for order 2 or 3 (Sec. II.C, App. A): q populations with
+ * velocities vel[q][3], energy levels, energies p0 and weights w.  The arrays are static and owned
+ * by the library.  Host-only; needs no GPU.  Errors: RLB_EINVAL for other orders. */
+rlb_status rlb_quadrature(int order, int* q, const int** vel, const int** level, const double** p0,
+                          const double** w);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RLB_H */

@@ -8,6 +8,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "rlb_oracle.c")
+HDR = os.path.join(HERE, "gs_basis.h")
 LIB = os.path.join(HERE, "_build", "librlb_oracle.so")
 LATTICE_DIR = os.path.join(os.path.dirname(HERE), "lattice")
 HBARC_GEV_FM = 0.1973269804
@@ -19,7 +20,8 @@ _lib = None
 def build(force=False):
     """Compile rlb_oracle.c (plain gcc, strict ISO C so no FMA contraction)."""
     os.makedirs(os.path.dirname(LIB), exist_ok=True)
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(SRC),
+                                                                       os.path.getmtime(HDR)):
         tmp = LIB + ".%d.tmp" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC", "-o", tmp, SRC, "-lm"])
         os.replace(tmp, LIB)
@@ -38,15 +40,21 @@ def _load():
             lib.ora_feq3_over_w.restype = d
             lib.ora_feq2_over_w.argtypes = [d, d, dp, d, d, d, d]
             lib.ora_feq2_over_w.restype = d
-            lib.ora_equilibrium_cell.argtypes = [i, i, ip, dp, dp, d, d, dp, dp]
+            lib.ora_equilibrium_cell.argtypes = [i, i, dp, dp, d, d, dp, dp]
+            lib.ora_equilibrium_appendix_cell.argtypes = [i, i, ip, dp, dp, d, d, dp, dp]
+            lib.ora_gs_table.argtypes = [i, i, ip, dp, dp]
+            lib.ora_gs_table.restype = i
             lib.ora_moments_cell.argtypes = [i, i, ip, dp, dp, dp, dp]
             lib.ora_landau_cell.argtypes = [dp, dp, dp, dp, dp]
             lib.ora_landau_cell.restype = i
             lib.ora_tau_prime.argtypes = [d, d, d, d]
             lib.ora_tau_prime.restype = d
-            lib.ora_step.argtypes = [i, i, ip, dp, dp, i, i, i, ip, d, d, i, d, d, d, i, i, dp, dp, dp, dp]
+            lib.ora_step.argtypes = [i, i, ip, dp, dp, dp, i, i, i, ip, d, d, i, d, d, d, i, i, dp, dp, dp, dp]
             lib.ora_step.restype = l
-            lib.ora_init.argtypes = [i, i, ip, dp, dp, l, dp, dp, dp, dp]
+            lib.ora_init_step_cells.argtypes = [i, i, ip, dp, dp, dp, i, i, i, ip, d, d, i, d, d, d, dp, dp, dp, l,
+                                                ctypes.POINTER(ctypes.c_long), dp]
+            lib.ora_init_step_cells.restype = l
+            lib.ora_init.argtypes = [i, i, dp, dp, l, dp, dp, dp, dp]
             lib.ora_init.restype = i
             _lib = lib
     return _lib
@@ -72,6 +80,17 @@ class Lattice:
         self.p0 = np.ascontiguousarray(p0, dtype=np.float64)
         self.w = np.ascontiguousarray(w, dtype=np.float64)
         self.q = len(self.w)
+        self._gs = None
+
+    @property
+    def gs(self):
+        """P_k(p_i) of the Gram-Schmidt basis for every population, shape (q, 30 or 14)."""
+        if self._gs is None:
+            nm = 30 if self.order == 3 else 14
+            tab = np.empty((self.q, nm))
+            _load().ora_gs_table(self.order, self.q, _ip(self.v), _dp(self.p0), _dp(tab))
+            self._gs = tab
+        return self._gs
 
     def momenta(self):
         """(q, 4) array of p_i^mu."""
@@ -108,11 +127,19 @@ def tau_prime(eta_over_s, R, T, dx_fm=0.008, T_unit_GeV=0.4):
 
 
 def equilibrium_cell(lat, n, T, U):
-    """f_i^eq of one cell from the appendix formula (Eq. (eq:equi3rd) / (eq:equi2nd))."""
+    """f_i^eq = w_i sum_k a_k J_k(p_i) of one cell (Eqs. (coeff), (eq:disc1))."""
     U = np.ascontiguousarray(U, dtype=np.float64)
     out = np.empty(lat.q)
-    _load().ora_equilibrium_cell(lat.order, lat.q, _ip(lat.v), _dp(lat.p0), _dp(lat.w), float(n), float(T),
-                                 _dp(U), _dp(out))
+    _load().ora_equilibrium_cell(lat.order, lat.q, _dp(lat.w), _dp(lat.gs), float(n), float(T), _dp(U), _dp(out))
+    return out
+
+
+def equilibrium_appendix_cell(lat, n, T, U):
+    """f_i^eq of one cell from the explicit App. B formula (Eq. (eq:equi3rd) / (eq:equi2nd))."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    out = np.empty(lat.q)
+    _load().ora_equilibrium_appendix_cell(lat.order, lat.q, _ip(lat.v), _dp(lat.p0), _dp(lat.w), float(n),
+                                          float(T), _dp(U), _dp(out))
     return out
 
 
@@ -161,8 +188,8 @@ class OracleRLB:
         T = np.ascontiguousarray(np.broadcast_to(T, self.shape), dtype=np.float64)
         u = np.ascontiguousarray(np.broadcast_to(u, (3,) + self.shape), dtype=np.float64)
         lat = self.lat
-        st = _load().ora_init(lat.order, lat.q, _ip(lat.v), _dp(lat.p0), _dp(lat.w), self.cells, _dp(n), _dp(T),
-                              _dp(u), _dp(self.f))
+        st = _load().ora_init(lat.order, lat.q, _dp(lat.w), _dp(lat.gs), self.cells, _dp(n), _dp(T), _dp(u),
+                              _dp(self.f))
         if st != 0:
             raise ValueError("invalid initial fields")
         self.prev, self.steps = None, 0
@@ -173,7 +200,8 @@ class OracleRLB:
 
     def _call(self, fin, fout, pull, collide, fields=None, dens=None):
         lat = self.lat
-        return _load().ora_step(lat.order, lat.q, _ip(lat.v), _dp(lat.p0), _dp(lat.w), self.nx, self.ny, self.nz,
+        return _load().ora_step(lat.order, lat.q, _ip(lat.v), _dp(lat.p0), _dp(lat.w), _dp(lat.gs), self.nx,
+                                self.ny, self.nz,
                                 _ip(self.bc), self.eta_over_s, self.tau_prime, self.tau_local_T, self.T_ref,
                                 self.dx_fm, self.T_unit_GeV, pull, collide, _dp(fin), _dp(fout), _dp(fields),
                                 _dp(dens))
@@ -185,6 +213,24 @@ class OracleRLB:
             self.prev, self.f = self.f, out
             self.steps += 1
         return self.nonconv
+
+    def init_step_cells(self, n, T, u, sample):
+        """Populations (len(sample), q) after one step from the equilibrium of (n, T, u), computed
+        only at the listed cells (flat indices, x fastest)."""
+        n = np.ascontiguousarray(np.broadcast_to(n, self.shape), dtype=np.float64)
+        T = np.ascontiguousarray(np.broadcast_to(T, self.shape), dtype=np.float64)
+        u = np.ascontiguousarray(np.broadcast_to(u, (3,) + self.shape), dtype=np.float64)
+        sample = np.ascontiguousarray(sample, dtype=np.int64)
+        out = np.empty((len(sample), self.lat.q))
+        lat = self.lat
+        bad = _load().ora_init_step_cells(
+            lat.order, lat.q, _ip(lat.v), _dp(lat.p0), _dp(lat.w), _dp(lat.gs), self.nx, self.ny, self.nz,
+            _ip(self.bc),
+            self.eta_over_s, self.tau_prime, self.tau_local_T, self.T_ref, self.dx_fm, self.T_unit_GeV, _dp(n),
+            _dp(T), _dp(u), len(sample), sample.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _dp(out))
+        if bad < 0:
+            raise ValueError("invalid fields")
+        return out
 
     def moments(self):
         """(n, eps, U[4], totals[5]) at the current time level; totals = sum N^0, T^00, T^0x, T^0y, T^0z."""

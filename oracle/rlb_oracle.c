@@ -12,8 +12,12 @@
  *   - Landau matching T^{a b} U_b = eps U^a, n = U_mu N^mu, eps = 3 n T (Eqs. (eigenproblem),
  *     (densitycal), Sec. II.D), solved by plain power iteration from the Eckart vector N/|N|;
  *   - relaxation time tau' from eta/s (Sec. II.D transport coefficients, Sec. III entropy);
- *   - discrete equilibrium f_i^eq = w_i * (explicit polynomial of App. B, Eq. (eq:equi3rd) for the
- *     third-order model, Eq. (eq:equi2nd) for the second-order model);
+ *   - discrete equilibrium f_i^eq = w_i sum_k a_k J_k(p_i) (Eq. (eq:disc1)) with the projections
+ *     a_k = int f^eq J_k d^3p/p0 (Eq. (coeff)) taken from the closed-form Maxwell-Juttner moments
+ *     and J_k the Gram-Schmidt polynomials of Sec. II.B (orders 0-3, or 0-2 for the second-order
+ *     model); the explicit App. B forms (Eqs. (eq:equi3rd), (eq:equi2nd)) are kept as a
+ *     cross-check: written out in powers of p they lose up to ~1e-12 to cancellation at T ~ 2 and
+ *     p0 ~ 11, the orthogonal-basis sum about 1e-14;
  *   - Anderson-Witting BGK collision f_i <- f_i - (p_i^mu U_mu)/(tau' p_i^0) (f_i - f_i^eq)
  *     (Eq. (rlb:disc), right-hand side, with delta t' = 1).
  *
@@ -25,6 +29,8 @@
 #include <stddef.h>
 #include <stdlib.h>
 #include <string.h>
+
+#include "gs_basis.h"
 
 #define ORA_QMAX 128
 #define ORA_HBARC_GEV_FM 0.1973269804 /* CODATA hbar*c, converts T*time into a pure number */
@@ -94,15 +100,96 @@ double ora_feq2_over_w(double n, double T, const double U[4], double p0, double 
   return n / (4.0 * T) * br;
 }
 
-/* f_i^eq for every population of one cell (Eq. (eq:disc1) through its explicit form). */
-void ora_equilibrium_cell(int order, int q, const int* v, const double* p0, const double* w, double n, double T,
-                          const double U[4], double* feq) {
+/* f_i^eq for every population of one cell through the explicit App. B form (cross-check only). */
+void ora_equilibrium_appendix_cell(int order, int q, const int* v, const double* p0, const double* w, double n,
+                                   double T, const double U[4], double* feq) {
   const double R = (order == 3) ? sqrt(41.0) : 3.0;
   for (int i = 0; i < q; ++i) {
     const double px = p0[i] * v[3 * i + 0] / R, py = p0[i] * v[3 * i + 1] / R, pz = p0[i] * v[3 * i + 2] / R;
     const double e = (order == 3) ? ora_feq3_over_w(n, T, U, p0[i], px, py, pz)
                                   : ora_feq2_over_w(n, T, U, p0[i], px, py, pz);
     feq[i] = w[i] * e;
+  }
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Equilibrium as the projection of Sec. II.B.  The orthogonal polynomials P_k (unnormalised J_k)
+ * come from exact Gram-Schmidt over the monomials p0^e px^a py^b pz^c (e <= 1) listed in
+ * gs_basis.h; a_k J_k(p) = (<f^eq, P_k> / <P_k, P_k>) P_k(p) with <f^eq, m> the Maxwell-Juttner
+ * moment of the monomial m.
+ * ------------------------------------------------------------------------------------------- */
+static int gs_size(int order) { return order == 3 ? ORA_GS3_N : ORA_GS2_N; }
+static const int (*gs_mono(int order))[4] { return order == 3 ? ora_gs3_mono : ora_gs2_mono; }
+static long double gs_coef(int order, int k, int j) { return order == 3 ? ora_gs3_coef[k][j] : ora_gs2_coef[k][j]; }
+static long double gs_norm(int order, int k) { return order == 3 ? ora_gs3_norm[k] : ora_gs2_norm[k]; }
+
+/* P_k(p_i) for every population (tab[i][k], i < q, k < gs_size), evaluated in long double and
+ * rounded once.  Returns the number of basis polynomials. */
+int ora_gs_table(int order, int q, const int* v, const double* p0, double* tab) {
+  const int nm = gs_size(order);
+  const int(*mono)[4] = gs_mono(order);
+  const long double R = sqrtl(order == 3 ? 41.0L : 9.0L);
+  for (int i = 0; i < q; ++i) {
+    const long double p[4] = {p0[i], p0[i] * (long double)v[3 * i] / R, p0[i] * (long double)v[3 * i + 1] / R,
+                              p0[i] * (long double)v[3 * i + 2] / R};
+    long double m[ORA_GS3_N];
+    for (int j = 0; j < nm; ++j) {
+      long double x = 1.0L;
+      for (int e = 0; e < mono[j][0]; ++e) x *= p[0];
+      for (int e = 0; e < mono[j][1]; ++e) x *= p[1];
+      for (int e = 0; e < mono[j][2]; ++e) x *= p[2];
+      for (int e = 0; e < mono[j][3]; ++e) x *= p[3];
+      m[j] = x;
+    }
+    for (int k = 0; k < nm; ++k) {
+      long double s = 0.0L;
+      for (int j = 0; j < nm; ++j) s += gs_coef(order, k, j) * m[j];
+      tab[(size_t)i * nm + k] = (double)s;
+    }
+  }
+  return nm;
+}
+
+/* Maxwell-Juttner moment of the monomial p0^e px^a py^b pz^c (degree <= 3) over d^3p/p0:
+ * n/(2T) for degree 0 (a Lorentz scalar, its rest-frame value), then N^mu = n U^mu,
+ * T^{mu nu} = -n T eta^{mu nu} + 4 n T U^mu U^nu, P^{mu nu l} = -4 n T^2 (eta^{mu nu} U^l +
+ * eta^{mu l} U^nu + eta^{nu l} U^mu) + 24 n T^2 U^mu U^nu U^l (Sec. II.C). */
+static double mj_moment(double n, double T, const double U[4], const int mono[4]) {
+  int idx[3], k = 0;
+  for (int e = 0; e < mono[0]; ++e) idx[k++] = 0;
+  for (int e = 0; e < mono[1]; ++e) idx[k++] = 1;
+  for (int e = 0; e < mono[2]; ++e) idx[k++] = 2;
+  for (int e = 0; e < mono[3]; ++e) idx[k++] = 3;
+#define ETA(a, b) ((a) != (b) ? 0.0 : ((a) == 0 ? 1.0 : -1.0))
+  switch (k) {
+    case 0: return n / (2.0 * T);
+    case 1: return n * U[idx[0]];
+    case 2: return -n * T * ETA(idx[0], idx[1]) + 4.0 * n * T * U[idx[0]] * U[idx[1]];
+    default:
+      return -4.0 * n * T * T *
+                 (ETA(idx[0], idx[1]) * U[idx[2]] + ETA(idx[0], idx[2]) * U[idx[1]] + ETA(idx[1], idx[2]) * U[idx[0]]) +
+             24.0 * n * T * T * U[idx[0]] * U[idx[1]] * U[idx[2]];
+  }
+#undef ETA
+}
+
+/* f_i^eq = w_i sum_k a_k J_k(p_i) for every population of one cell (Eqs. (coeff), (eq:disc1));
+ * gs = the table of ora_gs_table for this lattice. */
+void ora_equilibrium_cell(int order, int q, const double* w, const double* gs, double n, double T, const double U[4],
+                          double* feq) {
+  const int nm = gs_size(order);
+  const int(*mono)[4] = gs_mono(order);
+  double b[ORA_GS3_N], a[ORA_GS3_N];
+  for (int j = 0; j < nm; ++j) b[j] = mj_moment(n, T, U, mono[j]);
+  for (int k = 0; k < nm; ++k) {
+    double s = 0.0;
+    for (int j = 0; j < nm; ++j) s += (double)gs_coef(order, k, j) * b[j];
+    a[k] = s / (double)gs_norm(order, k); /* <f^eq, P_k> / <P_k, P_k> */
+  }
+  for (int i = 0; i < q; ++i) {
+    double s = 0.0;
+    for (int k = 0; k < nm; ++k) s += a[k] * gs[(size_t)i * nm + k];
+    feq[i] = w[i] * s;
   }
 }
 
@@ -175,6 +262,44 @@ static inline long wrap_index(long s, long n, int bc) {
   return s;
 }
 
+/* Moments, Landau matching, relaxation time, equilibrium and collision of one cell whose pulled
+ * populations are ft[q].  Writes fo[q] (if collide), fld[6] = n, eps, U0..U3 and dn[5] = N^0,
+ * T^00, T^0x, T^0y, T^0z (if non-NULL).  Returns ORA_OK or ORA_ENONCONV (then fo = ft, fld = NaN). */
+static int collide_cell(int order, int q, const int* v, const double* p0, const double* w, const double* gs,
+                        double eta_over_s,
+                        double tau_prime, int tau_local_T, double T_ref, double kappa, int collide,
+                        const double* ft, double* fo, double* fld, double* dn) {
+  const double R = (order == 3) ? sqrt(41.0) : 3.0;
+  double N[4], Tm[16], U[4], eps = NAN, n = NAN, feq[ORA_QMAX];
+  ora_moments_cell(order, q, v, p0, ft, N, Tm);
+  if (dn) {
+    dn[0] = N[0];
+    for (int b = 0; b < 4; ++b) dn[1 + b] = Tm[b];
+  }
+  if (ora_landau_cell(N, Tm, U, &eps, &n) != ORA_OK) {
+    if (fld)
+      for (int k = 0; k < 6; ++k) fld[k] = NAN;
+    if (collide)
+      for (int i = 0; i < q; ++i) fo[i] = ft[i];
+    return ORA_ENONCONV;
+  }
+  const double T = eps / (3.0 * n); /* equation of state eps = 3 n T */
+  if (fld) {
+    fld[0] = n;
+    fld[1] = eps;
+    for (int a = 0; a < 4; ++a) fld[2 + a] = U[a];
+  }
+  if (!collide) return ORA_OK;
+  const double tau = (tau_prime > 0.5) ? tau_prime : ora_tau_prime(eta_over_s, R, kappa, tau_local_T ? T : T_ref);
+  ora_equilibrium_cell(order, q, w, gs, n, T, U, feq);
+  for (int i = 0; i < q; ++i) {
+    /* p_i^mu U_mu / p_i^0 = U0 - (v_i . U) / R */
+    const double pu = U[0] - (v[3 * i] * U[1] + v[3 * i + 1] * U[2] + v[3 * i + 2] * U[3]) / R;
+    fo[i] = ft[i] - pu / tau * (ft[i] - feq[i]);
+  }
+  return ORA_OK;
+}
+
 /*
  * One time step on the whole lattice (Eq. (rlb:disc)): pull f~_i(x) = fin_i(x - v_i), moments,
  * Landau matching, tau', equilibrium, collision; writes fout.  If fields != NULL it receives the
@@ -185,15 +310,15 @@ static inline long wrap_index(long s, long n, int bc) {
  * reference temperature.  Returns the number of cells where Landau matching failed (those cells
  * are copied without collision and get NaN fields).
  */
-long ora_step(int order, int q, const int* v, const double* p0, const double* w, int nx, int ny, int nz,
+long ora_step(int order, int q, const int* v, const double* p0, const double* w, const double* gs, int nx, int ny,
+              int nz,
               const int* bc, double eta_over_s, double tau_prime, int tau_local_T, double T_ref, double dx_fm,
               double T_unit_GeV, int pull, int collide, const double* fin, double* fout, double* fields,
               double* dens) {
-  const double R = (order == 3) ? sqrt(41.0) : 3.0;
   const double kappa = T_unit_GeV * dx_fm / ORA_HBARC_GEV_FM;
   const size_t cells = (size_t)nx * ny * nz;
   long bad = 0;
-  double ft[ORA_QMAX], feq[ORA_QMAX];
+  double ft[ORA_QMAX], fo[ORA_QMAX], fld[6], dn[5];
   for (long z = 0; z < nz; ++z)
     for (long y = 0; y < ny; ++y)
       for (long x = 0; x < nx; ++x) {
@@ -207,43 +332,63 @@ long ora_step(int order, int q, const int* v, const double* p0, const double* w,
           }
           ft[i] = fin[(size_t)i * cells + ((size_t)sz * ny + sy) * nx + sx];
         }
-        double N[4], Tm[16], U[4], eps = NAN, n = NAN;
-        ora_moments_cell(order, q, v, p0, ft, N, Tm);
-        if (dens) {
-          dens[0 * cells + c] = N[0];
-          for (int b = 0; b < 4; ++b) dens[(1 + b) * cells + c] = Tm[b];
-        }
-        const int st = ora_landau_cell(N, Tm, U, &eps, &n);
-        if (st != ORA_OK) {
+        if (collide_cell(order, q, v, p0, w, gs, eta_over_s, tau_prime, tau_local_T, T_ref, kappa, collide, ft, fo,
+                         fld, dn) != ORA_OK)
           ++bad;
-          if (fields)
-            for (int k = 0; k < 6; ++k) fields[k * cells + c] = NAN;
-          if (collide)
-            for (int i = 0; i < q; ++i) fout[(size_t)i * cells + c] = ft[i];
-          continue;
-        }
-        const double T = eps / (3.0 * n); /* equation of state eps = 3 n T */
-        if (fields) {
-          fields[0 * cells + c] = n;
-          fields[1 * cells + c] = eps;
-          for (int a = 0; a < 4; ++a) fields[(2 + a) * cells + c] = U[a];
-        }
-        if (!collide) continue;
-        const double tau =
-            (tau_prime > 0.5) ? tau_prime : ora_tau_prime(eta_over_s, R, kappa, tau_local_T ? T : T_ref);
-        ora_equilibrium_cell(order, q, v, p0, w, n, T, U, feq);
-        for (int i = 0; i < q; ++i) {
-          /* p_i^mu U_mu / p_i^0 = U0 - (v_i . U) / R */
-          const double pu = U[0] - (v[3 * i] * U[1] + v[3 * i + 1] * U[2] + v[3 * i + 2] * U[3]) / R;
-          fout[(size_t)i * cells + c] = ft[i] - pu / tau * (ft[i] - feq[i]);
-        }
+        if (fields)
+          for (int k = 0; k < 6; ++k) fields[k * cells + c] = fld[k];
+        if (dens)
+          for (int k = 0; k < 5; ++k) dens[k * cells + c] = dn[k];
+        if (collide)
+          for (int i = 0; i < q; ++i) fout[(size_t)i * cells + c] = fo[i];
       }
   return bad;
 }
 
+/*
+ * Sampled cells of one step taken from the equilibrium of given fields: every population of the
+ * lattice starts as f_i^eq(n, T, u) of its cell; for each listed cell the populations after one
+ * step are written to out[k][q].  Needs only the fields (n, T double[cells], u double[3][cells]),
+ * so it can check single cells of lattices too large for ora_step.  Returns the number of listed
+ * cells where Landau matching failed, or -1 for invalid fields.
+ */
+long ora_init_step_cells(int order, int q, const int* v, const double* p0, const double* w, const double* gs, int nx,
+                         int ny, int nz,
+                         const int* bc, double eta_over_s, double tau_prime, int tau_local_T, double T_ref,
+                         double dx_fm, double T_unit_GeV, const double* n, const double* T, const double* u,
+                         long nsample, const long* sample, double* out) {
+  const double kappa = T_unit_GeV * dx_fm / ORA_HBARC_GEV_FM;
+  const size_t cells = (size_t)nx * ny * nz;
+  const int nm = gs_size(order);
+  long bad = 0;
+  double ft[ORA_QMAX], feq[ORA_QMAX];
+  for (long k = 0; k < nsample; ++k) {
+    const long c = sample[k];
+    const long x = c % nx, y = (c / nx) % ny, z = c / ((long)nx * ny);
+    for (int i = 0; i < q; ++i) {
+      const long sx = wrap_index(x - v[3 * i + 0], nx, bc[0]);
+      const long sy = wrap_index(y - v[3 * i + 1], ny, bc[1]);
+      const long sz = wrap_index(z - v[3 * i + 2], nz, bc[2]);
+      const size_t s = ((size_t)sz * ny + sy) * nx + sx;
+      const double ux = u[s], uy = u[cells + s], uz = u[2 * cells + s];
+      const double u2 = ux * ux + uy * uy + uz * uz;
+      if (!(u2 < 1.0) || !(T[s] > 0.0) || !(n[s] > 0.0)) return -1;
+      const double g = 1.0 / sqrt(1.0 - u2);
+      const double U[4] = {g, g * ux, g * uy, g * uz};
+      /* population i of the source cell: its equilibrium, evaluated for that population only */
+      ora_equilibrium_cell(order, 1, w + i, gs + (size_t)i * nm, n[s], T[s], U, feq);
+      ft[i] = feq[0];
+    }
+    if (collide_cell(order, q, v, p0, w, gs, eta_over_s, tau_prime, tau_local_T, T_ref, kappa, 1, ft, out + k * q,
+                     NULL, NULL) != ORA_OK)
+      ++bad;
+  }
+  return bad;
+}
+
 /* f_i = f_i^eq(n, T, u) on every cell; U = gamma (1, u).  Returns ORA_EINVAL if |u| >= 1. */
-int ora_init(int order, int q, const int* v, const double* p0, const double* w, long cells, const double* n,
-             const double* T, const double* u, double* f) {
+int ora_init(int order, int q, const double* w, const double* gs, long cells, const double* n, const double* T,
+             const double* u, double* f) {
   double feq[ORA_QMAX];
   for (long c = 0; c < cells; ++c) {
     const double ux = u[c], uy = u[cells + c], uz = u[2 * cells + c];
@@ -251,7 +396,7 @@ int ora_init(int order, int q, const int* v, const double* p0, const double* w, 
     if (!(u2 < 1.0) || !(T[c] > 0.0) || !(n[c] > 0.0)) return ORA_EINVAL;
     const double g = 1.0 / sqrt(1.0 - u2);
     const double U[4] = {g, g * ux, g * uy, g * uz};
-    ora_equilibrium_cell(order, q, v, p0, w, n[c], T[c], U, feq);
+    ora_equilibrium_cell(order, q, w, gs, n[c], T[c], U, feq);
     for (int i = 0; i < q; ++i) f[(size_t)i * cells + c] = feq[i];
   }
   return ORA_OK;

@@ -1,0 +1,367 @@
+// C ABI of librlb (declared in include/rlb.h): context management, validation, kernel launches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "rlb.h"
+#include "rlb_common.h"
+#include "rlb_launch.h"
+#include "rlb_quadrature.h"
+
+using namespace rlb;
+
+namespace {
+
+constexpr double kHbarcGeVfm = 0.1973269804;  // CODATA hbar*c: (GeV * fm/c) -> pure number
+
+template <class L>
+struct QuadHost {
+  int vel[L::Q * 3], level[L::Q];
+  double p0[L::Q], w[L::Q];
+  QuadHost() {
+    for (int i = 0; i < L::Q; ++i) {
+      vel[3 * i] = L::VX[i];
+      vel[3 * i + 1] = L::VY[i];
+      vel[3 * i + 2] = L::VZ[i];
+      level[i] = L::LEV[i];
+      p0[i] = L::P0[L::LEV[i]];
+      w[i] = L::W[i];
+    }
+  }
+};
+const QuadHost<Quad3> kQuad3;
+const QuadHost<Quad2> kQuad2;
+
+size_t storage_bytes(int storage) { return storage == RLB_F64 ? 8 : (storage == RLB_F32 ? 4 : 2); }
+
+}  // namespace
+
+struct rlb_ctx {
+  rlb_params prm;
+  int q = 0;
+  int cells = 0;
+  size_t elem = 0;
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;              // buf[cur] holds the current (post-collision) state
+  bool have_prev = false;   // buf[1 - cur] holds the state the last step pulled from
+  long steps = 0;
+  long launches = 0;
+  cudaStream_t stream = nullptr;
+  StepParams sp;
+  bool general_wrap = false;
+  double* fields = nullptr;   // 6 * cells; also staging for host inputs
+  double* partial = nullptr;  // 5 * blocks
+  double* totals = nullptr;   // 5
+  int* status = nullptr;      // kStatusWords
+  int fblocks = 0;
+  const Launchers* launch = nullptr;
+  std::string err;
+};
+
+// Errors of calls that have no context (rlb_create with invalid parameters) are kept per thread.
+static thread_local std::string g_create_err;
+
+static rlb_status fail(rlb_ctx* c, rlb_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_create_err = msg;
+  return st;
+}
+
+static rlb_status cuda_fail(rlb_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, RLB_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define RLB_CUDA(ctx, call)                                        \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);     \
+  } while (0)
+
+extern "C" void rlb_default_params(rlb_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->order = 3;
+  p->nx = p->ny = p->nz = 1;
+  p->eta_over_s = 0.1;
+  p->tau_prime = 0.0;
+  p->tau_local_T = 1;
+  p->T_ref = 1.0;
+  p->dx_fm = 0.008;
+  p->T_unit_GeV = 0.4;
+  p->storage = RLB_F64;
+  p->landau_fp64 = 0;
+  p->gamma_thr = 2.0;
+  p->n_ref = 1.0;
+}
+
+extern "C" rlb_status rlb_quadrature(int order, int* q, const int** vel, const int** level, const double** p0,
+                                     const double** w) {
+  if (order != 2 && order != 3) return RLB_EINVAL;
+  const bool o3 = order == 3;
+  if (q) *q = o3 ? Quad3::Q : Quad2::Q;
+  if (vel) *vel = o3 ? kQuad3.vel : kQuad2.vel;
+  if (level) *level = o3 ? kQuad3.level : kQuad2.level;
+  if (p0) *p0 = o3 ? kQuad3.p0 : kQuad2.p0;
+  if (w) *w = o3 ? kQuad3.w : kQuad2.w;
+  return RLB_OK;
+}
+
+static std::string validate(const rlb_params* p) {
+  if (!p) return "params is NULL";
+  if (p->order != 2 && p->order != 3) return "order must be 2 or 3";
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return "lattice dimensions must be >= 1";
+  const long long cells = (long long)p->nx * p->ny * p->nz;
+  if (cells > 0x7fffffffll) return "more than 2^31 - 1 cells";
+  for (int a = 0; a < 3; ++a)
+    if (p->bc[a] != RLB_BC_PERIODIC && p->bc[a] != RLB_BC_COPYOUT) return "bc must be periodic or copy-out";
+  if (p->storage != RLB_F64 && p->storage != RLB_F32 && p->storage != RLB_F16DEV) return "unknown storage";
+  if (!(p->tau_prime > 0.5)) {
+    if (!(p->eta_over_s > 0) || !std::isfinite(p->eta_over_s)) return "eta_over_s must be > 0 (or tau_prime > 1/2)";
+    if (!(p->dx_fm > 0) || !(p->T_unit_GeV > 0)) return "dx_fm and T_unit_GeV must be > 0";
+    if (!p->tau_local_T && !(p->T_ref > 0)) return "T_ref must be > 0";
+  } else if (!std::isfinite(p->tau_prime)) {
+    return "tau_prime must be finite";
+  }
+  if (!(p->gamma_thr >= 1.0)) return "gamma_thr must be >= 1";
+  if (p->storage == RLB_F16DEV && !(p->n_ref > 0)) return "n_ref must be > 0";
+  if (p->q > 0) {
+    int q;
+    const int *vel, *lev;
+    const double *p0, *w;
+    rlb_quadrature(p->order, &q, &vel, &lev, &p0, &w);
+    if (p->q != q) return "quadrature size differs from the built-in one";
+    if (!p->vel || !p->level || !p->p0 || !p->w) return "quadrature arrays missing";
+    for (int i = 0; i < q; ++i) {
+      if (p->vel[3 * i] != vel[3 * i] || p->vel[3 * i + 1] != vel[3 * i + 1] || p->vel[3 * i + 2] != vel[3 * i + 2] ||
+          p->level[i] != lev[i] || p->p0[i] != p0[i] || p->w[i] != w[i])
+        return "quadrature differs from the built-in one at population " + std::to_string(i);
+    }
+  }
+  return "";
+}
+
+extern "C" size_t rlb_bytes_required(const rlb_params* p) {
+  if (!validate(p).empty()) return 0;
+  const size_t cells = (size_t)p->nx * p->ny * p->nz;
+  const size_t q = p->order == 3 ? Quad3::Q : Quad2::Q;
+  const size_t blocks = (cells + kMomThreads - 1) / kMomThreads;
+  return 2 * q * cells * storage_bytes(p->storage) + 6 * cells * sizeof(double) + 5 * blocks * sizeof(double) +
+         5 * sizeof(double) + kStatusWords * sizeof(int);
+}
+
+template <class L>
+static void fill_offsets(StepParams& sp) {
+  for (int i = 0; i < L::Q; ++i)
+    sp.off[i] = (long long)i * sp.cells - ((long long)L::VX[i] + (long long)L::VY[i] * sp.nx +
+                                           (long long)L::VZ[i] * sp.nxy);
+}
+
+template <class L>
+static bool needs_general_wrap(const rlb_params& p) {
+  return (p.bc[0] == RLB_BC_PERIODIC && p.nx < L::VMAX_X) || (p.bc[1] == RLB_BC_PERIODIC && p.ny < L::VMAX_Y) ||
+         (p.bc[2] == RLB_BC_PERIODIC && p.nz < L::VMAX_Z);
+}
+
+extern "C" rlb_status rlb_create(const rlb_params* p, rlb_ctx** out) {
+  if (!out) return fail(nullptr, RLB_EINVAL, "rlb_create: out is NULL");
+  *out = nullptr;
+  const std::string why = validate(p);
+  if (!why.empty()) return fail(nullptr, RLB_EINVAL, "rlb_create: " + why);
+  rlb_ctx* c = new (std::nothrow) rlb_ctx();
+  if (!c) return fail(nullptr, RLB_ENOMEM, "rlb_create: out of host memory");
+  c->prm = *p;
+  c->prm.vel = nullptr;
+  c->prm.level = nullptr;
+  c->prm.p0 = nullptr;
+  c->prm.w = nullptr;
+  c->q = p->order == 3 ? Quad3::Q : Quad2::Q;
+  c->cells = p->nx * p->ny * p->nz;
+  c->elem = storage_bytes(p->storage);
+  c->stream = (cudaStream_t)p->stream;
+
+  StepParams& sp = c->sp;
+  std::memset(&sp, 0, sizeof(sp));
+  sp.nx = p->nx;
+  sp.ny = p->ny;
+  sp.nz = p->nz;
+  sp.nxy = p->nx * p->ny;
+  sp.cells = c->cells;
+  for (int a = 0; a < 3; ++a) sp.bc[a] = p->bc[a];
+  const double R = p->order == 3 ? Quad3::R : Quad2::R;
+  sp.tau_fixed = p->tau_prime > 0.5 ? p->tau_prime : 0.0;
+  const double kappa = p->T_unit_GeV * p->dx_fm / kHbarcGeVfm;
+  sp.tau_coef = (p->tau_prime > 0.5) ? 0.0 : 6.0 * p->eta_over_s / (R * kappa);
+  sp.tau_local = p->tau_local_T ? 1 : 0;
+  sp.T_ref = p->T_ref;
+  sp.gamma_thr2 = (float)(p->gamma_thr * p->gamma_thr);
+  sp.landau_fp64 = p->landau_fp64 ? 1 : 0;
+  sp.half_nref = (float)(0.5 * p->n_ref);
+  static const Launchers* const table[2][3] = {{&launchers_o2_s0, &launchers_o2_s1, &launchers_o2_s2},
+                                               {&launchers_o3_s0, &launchers_o3_s1, &launchers_o3_s2}};
+  c->launch = table[p->order == 3 ? 1 : 0][p->storage];
+  if (p->order == 3) {
+    fill_offsets<Quad3>(sp);
+    c->general_wrap = needs_general_wrap<Quad3>(*p);
+  } else {
+    fill_offsets<Quad2>(sp);
+    c->general_wrap = needs_general_wrap<Quad2>(*p);
+  }
+
+  const size_t pop_bytes = (size_t)c->q * c->cells * c->elem;
+  c->fblocks = (c->cells + kMomThreads - 1) / kMomThreads;
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&c->buf[b], pop_bytes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->fields, 6 * (size_t)c->cells * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->partial, 5 * (size_t)c->fblocks * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->totals, 5 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->status, kStatusWords * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, kStatusWords * sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->buf[0], 0, pop_bytes, c->stream);
+  if (e != cudaSuccess) {
+    const rlb_status st = (e == cudaErrorMemoryAllocation) ? RLB_ENOMEM : RLB_ECUDA;
+    cudaGetLastError();
+    rlb_destroy(c);
+    return fail(nullptr, st, std::string("rlb_create: ") + cudaGetErrorString(e));
+  }
+  *out = c;
+  return RLB_OK;
+}
+
+extern "C" rlb_status rlb_destroy(rlb_ctx* c) {
+  if (!c) return RLB_OK;
+  if (c->stream || c->buf[0]) cudaStreamSynchronize(c->stream);
+  for (int b = 0; b < 2; ++b)
+    if (c->buf[b]) cudaFree(c->buf[b]);
+  if (c->fields) cudaFree(c->fields);
+  if (c->partial) cudaFree(c->partial);
+  if (c->totals) cudaFree(c->totals);
+  if (c->status) cudaFree(c->status);
+  delete c;
+  return RLB_OK;
+}
+
+extern "C" const char* rlb_last_error(const rlb_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+extern "C" long rlb_steps_done(const rlb_ctx* c) { return c ? c->steps : -1; }
+extern "C" long rlb_kernel_launches(const rlb_ctx* c) { return c ? c->launches : -1; }
+
+static rlb_status check_launch(rlb_ctx* c, cudaError_t e, const char* what) {
+  ++c->launches;
+  if (e != cudaSuccess) return cuda_fail(c, e, what);
+  return RLB_OK;
+}
+
+static rlb_status read_status(rlb_ctx* c) {
+  int st[kStatusWords];
+  RLB_CUDA(c, cudaMemcpyAsync(st, c->status, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+  RLB_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (st[kStatusBadInit] > 0) {
+    RLB_CUDA(c, cudaMemsetAsync(c->status, 0, kStatusWords * sizeof(int), c->stream));
+    return fail(c, RLB_EINVAL, std::to_string(st[kStatusBadInit]) + " cells with invalid initial fields");
+  }
+  if (st[kStatusNonconv] > 0) {
+    RLB_CUDA(c, cudaMemsetAsync(c->status, 0, kStatusWords * sizeof(int), c->stream));
+    return fail(c, RLB_ENONCONV, std::to_string(st[kStatusNonconv]) + " cell updates without a Landau frame");
+  }
+  return RLB_OK;
+}
+
+extern "C" rlb_status rlb_sync(rlb_ctx* c) {
+  if (!c) return RLB_EINVAL;
+  return read_status(c);
+}
+
+extern "C" rlb_status rlb_init(rlb_ctx* c, const double* n, const double* T, const double* u, int on_device) {
+  if (!c) return RLB_EINVAL;
+  if (!n || !T || !u) return fail(c, RLB_EINVAL, "rlb_init: null field pointer");
+  const size_t cb = (size_t)c->cells * sizeof(double);
+  const double *dn = n, *dT = T, *du = u;
+  if (!on_device) {
+    RLB_CUDA(c, cudaMemcpyAsync(c->fields, n, cb, cudaMemcpyHostToDevice, c->stream));
+    RLB_CUDA(c, cudaMemcpyAsync(c->fields + c->cells, T, cb, cudaMemcpyHostToDevice, c->stream));
+    RLB_CUDA(c, cudaMemcpyAsync(c->fields + 2 * (size_t)c->cells, u, 3 * cb, cudaMemcpyHostToDevice, c->stream));
+    dn = c->fields;
+    dT = c->fields + c->cells;
+    du = c->fields + 2 * (size_t)c->cells;
+  }
+  rlb_status st =
+      check_launch(c, c->launch->init(dn, dT, du, c->buf[c->cur], c->sp, c->status, c->stream), "init kernel");
+  if (st != RLB_OK) return st;
+  if (!on_device) RLB_CUDA(c, cudaStreamSynchronize(c->stream));  // host buffers may be reused
+  c->steps = 0;
+  c->have_prev = false;
+  return RLB_OK;
+}
+
+extern "C" rlb_status rlb_step(rlb_ctx* c, long nsteps) {
+  if (!c) return RLB_EINVAL;
+  if (nsteps < 0) return fail(c, RLB_EINVAL, "nsteps < 0");
+  for (long s = 0; s < nsteps; ++s) {
+    rlb_status st = check_launch(
+        c, c->launch->step(c->buf[c->cur], c->buf[1 - c->cur], c->sp, c->status, c->general_wrap, c->stream),
+        "step kernel");
+    if (st != RLB_OK) return st;
+    c->cur = 1 - c->cur;
+    c->have_prev = true;
+    ++c->steps;
+  }
+  return RLB_OK;
+}
+
+extern "C" rlb_status rlb_moments(rlb_ctx* c, double* n, double* eps, double* U, double totals[5], int on_device) {
+  if (!c) return RLB_EINVAL;
+  const bool pull = c->have_prev;
+  const void* src = pull ? c->buf[1 - c->cur] : c->buf[c->cur];
+  rlb_status st = check_launch(
+      c, c->launch->fields(src, c->sp, c->fields, c->partial, c->status, pull, c->stream), "fields kernel");
+  if (st != RLB_OK) return st;
+  st = check_launch(c, launch_reduce_partials(c->partial, c->fblocks, c->totals, c->stream), "reduce kernel");
+  if (st != RLB_OK) return st;
+  const size_t cb = (size_t)c->cells * sizeof(double);
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (n) RLB_CUDA(c, cudaMemcpyAsync(n, c->fields, cb, k, c->stream));
+  if (eps) RLB_CUDA(c, cudaMemcpyAsync(eps, c->fields + c->cells, cb, k, c->stream));
+  if (U) RLB_CUDA(c, cudaMemcpyAsync(U, c->fields + 2 * (size_t)c->cells, 4 * cb, k, c->stream));
+  if (totals) RLB_CUDA(c, cudaMemcpyAsync(totals, c->totals, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return read_status(c);
+}
+
+// Populations cross the boundary as double[q][cells].  Host transfers are staged one population
+// plane at a time through the field buffer (6 * cells doubles), device transfers convert in place.
+static rlb_status convert(rlb_ctx* c, double* dbl, int on_device, bool to_f64) {
+  void* pop = c->buf[c->cur];
+  const size_t cb = (size_t)c->cells * sizeof(double);
+  auto launch = [&](double* d, int i0, int i1) {
+    return check_launch(c, c->launch->convert(pop, d, i0, i1, to_f64, c->sp, c->stream), "convert kernel");
+  };
+  if (on_device) return launch(dbl, 0, c->q);
+  for (int i = 0; i < c->q; ++i) {
+    double* h = dbl + (size_t)i * c->cells;
+    if (!to_f64) RLB_CUDA(c, cudaMemcpyAsync(c->fields, h, cb, cudaMemcpyHostToDevice, c->stream));
+    rlb_status st = launch(c->fields, i, i + 1);
+    if (st != RLB_OK) return st;
+    if (to_f64) RLB_CUDA(c, cudaMemcpyAsync(h, c->fields, cb, cudaMemcpyDeviceToHost, c->stream));
+    RLB_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  return RLB_OK;
+}
+
+extern "C" rlb_status rlb_get_populations(rlb_ctx* c, double* f, int on_device) {
+  if (!c) return RLB_EINVAL;
+  if (!f) return fail(c, RLB_EINVAL, "rlb_get_populations: null pointer");
+  rlb_status st = convert(c, f, on_device, true);
+  if (st != RLB_OK) return st;
+  return read_status(c);
+}
+
+extern "C" rlb_status rlb_set_populations(rlb_ctx* c, const double* f, int on_device) {
+  if (!c) return RLB_EINVAL;
+  if (!f) return fail(c, RLB_EINVAL, "rlb_set_populations: null pointer");
+  rlb_status st = convert(c, const_cast<double*>(f), on_device, false);
+  if (st != RLB_OK) return st;
+  c->steps = 0;
+  c->have_prev = false;
+  return RLB_OK;
+}

@@ -1,0 +1,28 @@
+// Definitions shared by the host-side C ABI and the kernels.
+#pragma once
+
+namespace rlb {
+
+constexpr int kStepThreads = 128;    // threads per block of the step kernel (one cell each)
+constexpr int kMomThreads = 128;     // threads per block of the fields kernel
+constexpr int kReduceThreads = 256;  // threads of the single-block second reduction pass
+
+// ---------------------------------------------------------------------------------------------
+// launch parameters
+// ---------------------------------------------------------------------------------------------
+struct StepParams {
+  int nx, ny, nz, nxy, cells;
+  int bc[3];                // 0 periodic, 1 copy-out
+  long long off[128];       // interior pull offset of population i: i*cells - (vx + vy*nx + vz*nxy)
+  double tau_fixed;         // > 0.5: constant tau'
+  double tau_coef;          // tau' = 1/2 + tau_coef / T
+  int tau_local;            // T = local Landau temperature (1) or T_ref (0)
+  double T_ref;
+  float gamma_thr2;         // reduced-precision paths: Landau in double above this gamma^2
+  int landau_fp64;
+  float half_nref;          // F16DEV: n_ref / 2
+};
+
+enum : int { kStatusNonconv = 0, kStatusBadInit = 1, kStatusWords = 4 };
+
+}  // namespace rlb

@@ -1,0 +1,104 @@
+// Kernel instantiation for one (order, storage) pair, selected at compile time by
+// RLB_INST_ORDER (2 or 3) and RLB_INST_STORAGE (0 = double, 1 = float, 2 = half deviation).
+#include "rlb_kernels.cuh"
+#include "rlb_launch.h"
+
+#ifndef RLB_INST_ORDER
+#error "RLB_INST_ORDER must be defined"
+#endif
+#ifndef RLB_INST_STORAGE
+#error "RLB_INST_STORAGE must be defined"
+#endif
+
+namespace rlb {
+namespace {
+
+#if RLB_INST_ORDER == 3
+using L = Quad3;
+#else
+using L = Quad2;
+#endif
+#if RLB_INST_STORAGE == 0
+using S = StoreF64;
+#elif RLB_INST_STORAGE == 1
+using S = StoreF32;
+#else
+using S = StoreF16Dev;
+#endif
+using T = typename S::T;
+
+cudaError_t step(const void* src, void* dst, const StepParams& p, int* status, bool general, cudaStream_t s) {
+  const int blocks = (p.cells + kStepThreads - 1) / kStepThreads;
+  if (general)
+    k_step<L, S, true><<<blocks, kStepThreads, 0, s>>>((const T*)src, (T*)dst, p, status);
+  else
+    k_step<L, S, false><<<blocks, kStepThreads, 0, s>>>((const T*)src, (T*)dst, p, status);
+  return cudaGetLastError();
+}
+
+cudaError_t fields(const void* src, const StepParams& p, double* f, double* partial, int* status, bool pull,
+                   cudaStream_t s) {
+  const int blocks = (p.cells + kMomThreads - 1) / kMomThreads;
+  if (pull)
+    k_fields<L, S, true><<<blocks, kMomThreads, 0, s>>>((const T*)src, p, f, partial, status);
+  else
+    k_fields<L, S, false><<<blocks, kMomThreads, 0, s>>>((const T*)src, p, f, partial, status);
+  return cudaGetLastError();
+}
+
+cudaError_t init(const double* n, const double* Tf, const double* u, void* dst, const StepParams& p, int* status,
+                 cudaStream_t s) {
+  const int blocks = (p.cells + 127) / 128;
+  k_init<L, S><<<blocks, 128, 0, s>>>(n, Tf, u, (T*)dst, p, status);
+  return cudaGetLastError();
+}
+
+cudaError_t convert_pops(void* pop, double* dbl, int i0, int i1, bool to_f64, const StepParams& p, cudaStream_t s) {
+  const int blocks = (p.cells + 127) / 128;
+  if (to_f64)
+    k_convert<L, S, true><<<blocks, 128, 0, s>>>((T*)pop, dbl, 0, i0, i1, p);
+  else
+    k_convert<L, S, false><<<blocks, 128, 0, s>>>((T*)pop, dbl, 0, i0, i1, p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+#define RLB_CAT_(a, b, c, d) a##b##c##d
+#define RLB_NAME(o, s) RLB_CAT_(launchers_o, o, _s, s)
+extern const Launchers RLB_NAME(RLB_INST_ORDER, RLB_INST_STORAGE) = {step, fields, init, convert_pops};
+
+#if RLB_INST_ORDER == 3 && RLB_INST_STORAGE == 0
+// Second pass of the conserved-density sums: one block adds the per-block partials in a fixed
+// order (thread t takes blocks t, t + 256, ...; then a shuffle and shared-memory tree), so the
+// totals are bitwise reproducible.
+__global__ void __launch_bounds__(kReduceThreads) k_reduce_partials(const double* __restrict__ partial, int nblocks,
+                                                                     double* __restrict__ totals) {
+  __shared__ double ws[kReduceThreads / 32][5];
+  double d[5] = {0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nblocks; b += kReduceThreads)
+#pragma unroll
+    for (int k = 0; k < 5; ++k) d[k] += partial[(long long)b * 5 + k];
+#pragma unroll
+  for (int k = 0; k < 5; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d[k] += __shfl_down_sync(0xffffffffu, d[k], o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < 5; ++k) ws[warp][k] = d[k];
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    double s = 0.0;
+    for (int w = 0; w < kReduceThreads / 32; ++w) s += ws[w][threadIdx.x];
+    totals[threadIdx.x] = s;
+  }
+}
+
+
+cudaError_t launch_reduce_partials(const double* partial, int nblocks, double* totals, cudaStream_t s) {
+  k_reduce_partials<<<1, kReduceThreads, 0, s>>>(partial, nblocks, totals);
+  return cudaGetLastError();
+}
+#endif
+}  // namespace rlb

@@ -1,0 +1,564 @@
+// Kernels of the relativistic lattice Boltzmann step (arXiv:1301.3423) for sm_103a.
+//
+// One thread owns one cell.  A step (Eq. (rlb:disc)) is a single fused pass per cell:
+//   pull    f~_i(x) = f_i(x - v_i)                     one read per population
+//   moments N^mu, T^{mu nu} over mirror pairs         (Sec. II.D)
+//   Landau  T^{ab} U_b = eps U^a, n = U.N, T = eps/(3n) (Eq. (eigenproblem))
+//   tau'    from eta/s and T                           (Sec. II.D, Sec. III)
+//   f^eq    factored equilibrium, E(p0, t) with t = v.U/R   (App. B, Eq. (eq:equi3rd) / (eq:equi2nd))
+//   collide f_i - (U0 - t_i)/tau' (f_i - w_i E_i)      one write per population
+//
+// The quadrature is a compile-time table (generated rlb_quadrature.h), so every per-population
+// constant (velocity components, energy, weight, mirror partner) is an immediate.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+#include <utility>
+
+#include "rlb_common.h"
+#include "rlb_quadrature.h"
+
+namespace rlb {
+
+// ---------------------------------------------------------------------------------------------
+// compile-time loop
+// ---------------------------------------------------------------------------------------------
+template <int... Is, class F>
+__device__ __forceinline__ void sfor_impl(std::integer_sequence<int, Is...>, F& f) {
+  (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  sfor_impl(std::make_integer_sequence<int, N>{}, f);
+}
+template <int I>
+using ic = std::integral_constant<int, I>;
+
+// ---------------------------------------------------------------------------------------------
+// storage formats
+// ---------------------------------------------------------------------------------------------
+struct StoreF64 {
+  using T = double;
+  using A = double;                 // arithmetic of the step
+  static constexpr bool kKeep = false;  // 128 doubles do not fit the register file: reload
+  template <class L, int I>
+  __device__ static __forceinline__ A load(const T* p, const StepParams&) { return __ldg(p); }
+  template <class L, int I>
+  __device__ static __forceinline__ void store(T* p, A v, const StepParams&) { *p = v; }
+  template <class L, int I>
+  __device__ static __forceinline__ double to_f64(T v, const StepParams&) { return v; }
+  template <class L, int I>
+  __device__ static __forceinline__ T from_f64(double v, const StepParams&) { return v; }
+};
+
+struct StoreF32 {
+  using T = float;
+  using A = float;
+  static constexpr bool kKeep = true;   // all populations of a cell live in registers
+  template <class L, int I>
+  __device__ static __forceinline__ A load(const T* p, const StepParams&) { return __ldg(p); }
+  template <class L, int I>
+  __device__ static __forceinline__ void store(T* p, A v, const StepParams&) { *p = v; }
+  template <class L, int I>
+  __device__ static __forceinline__ double to_f64(T v, const StepParams&) { return (double)v; }
+  template <class L, int I>
+  __device__ static __forceinline__ T from_f64(double v, const StepParams&) { return (float)v; }
+};
+
+// Half-precision deviation d_i = f_i / w_i - n_ref / 2 from the weight-scaled rest equilibrium.
+struct StoreF16Dev {
+  using T = __half;
+  using A = float;
+  static constexpr bool kKeep = true;
+  template <class L, int I>
+  __device__ static __forceinline__ A load(const T* p, const StepParams& sp) {
+    constexpr float w = (float)L::W[I];
+    return w * (__half2float(__ldg(p)) + sp.half_nref);
+  }
+  template <class L, int I>
+  __device__ static __forceinline__ void store(T* p, A v, const StepParams& sp) {
+    constexpr float iw = (float)(1.0 / L::W[I]);
+    *p = __float2half_rn(fmaf(v, iw, -sp.half_nref));
+  }
+  template <class L, int I>
+  __device__ static __forceinline__ double to_f64(T v, const StepParams& sp) {
+    constexpr double w = L::W[I];
+    return w * ((double)__half2float(v) + (double)sp.half_nref);
+  }
+  template <class L, int I>
+  __device__ static __forceinline__ T from_f64(double v, const StepParams& sp) {
+    constexpr double iw = 1.0 / L::W[I];
+    return __float2half_rn((float)(v * iw - (double)sp.half_nref));
+  }
+};
+
+// ---------------------------------------------------------------------------------------------
+// cell geometry and the pull source index
+// ---------------------------------------------------------------------------------------------
+struct Cell {
+  int c, x, y, z;
+};
+
+__device__ __forceinline__ Cell make_cell(int c, const StepParams& p) {
+  Cell r;
+  r.c = c;
+  const int yz = c / p.nx;
+  r.x = c - yz * p.nx;
+  r.z = yz / p.ny;
+  r.y = yz - r.z * p.ny;
+  return r;
+}
+
+// Source coordinate of x - v along an axis of n cells: periodic wrap or copy-out clamp.
+// GENERAL handles n < |v| (a full modulo); otherwise one conditional wrap suffices.
+template <int V, bool GENERAL>
+__device__ __forceinline__ int src_coord(int x, int n, int bc) {
+  if constexpr (V == 0) {
+    return x;
+  } else {
+    int s = x - V;
+    if (bc) return (V > 0) ? max(s, 0) : min(s, n - 1);
+    if constexpr (GENERAL) {
+      s %= n;
+      return s < 0 ? s + n : s;
+    } else {
+      if constexpr (V > 0) return s < 0 ? s + n : s;
+      else return s >= n ? s - n : s;
+    }
+  }
+}
+
+template <class L, int I, bool GENERAL>
+__device__ __forceinline__ long long pull_index(const Cell& cl, const StepParams& p) {
+  constexpr int vx = L::VX[I], vy = L::VY[I], vz = L::VZ[I];
+  const int sx = src_coord<vx, GENERAL>(cl.x, p.nx, p.bc[0]);
+  const int sy = src_coord<vy, GENERAL>(cl.y, p.ny, p.bc[1]);
+  const int sz = src_coord<vz, GENERAL>(cl.z, p.nz, p.bc[2]);
+  return (long long)I * p.cells + (long long)(sz * p.nxy + sy * p.nx + sx);
+}
+
+template <class L>
+__device__ __forceinline__ bool is_interior(const Cell& cl, const StepParams& p) {
+  return cl.x >= L::VMAX_X && cl.x < p.nx - L::VMAX_X && cl.y >= L::VMAX_Y && cl.y < p.ny - L::VMAX_Y &&
+         cl.z >= L::VMAX_Z && cl.z < p.nz - L::VMAX_Z;
+}
+
+// ---------------------------------------------------------------------------------------------
+// moments N^mu, T^{mu nu} (Eqs. (moments:dis1), (moments:dis2)), accumulated over mirror pairs:
+// for a pair (v, -v) at energy p0, s1 = p0 (f+ +- f-), s2 = p0^2 (f+ +- f-).
+// ---------------------------------------------------------------------------------------------
+template <class A>
+struct Mom {
+  A N0, Nx, Ny, Nz, T00, T0x, T0y, T0z, Txx, Tyy, Tzz, Txy, Txz, Tyz;
+};
+
+template <class L, class A, class Get>
+__device__ __forceinline__ Mom<A> moments(Get&& get) {
+  Mom<A> m;
+  m.N0 = m.Nx = m.Ny = m.Nz = A(0);
+  m.T00 = m.T0x = m.T0y = m.T0z = A(0);
+  m.Txx = m.Tyy = m.Txy = m.Txz = m.Tyz = A(0);
+  static_for<L::NDP>([&](auto K) {
+    constexpr int k = decltype(K)::value;
+    constexpr int first = L::DP_FIRST[k];
+    constexpr int np = L::DP_NPAIR[k];
+    A s1p = A(0), s1m = A(0), s2p = A(0), s2m = A(0);
+    static_for<np>([&](auto J) {
+      constexpr int ip = first + 2 * decltype(J)::value;
+      constexpr double p0 = L::P0[L::LEV[ip]];
+      const A fa = get(ic<ip>{});
+      const A fb = get(ic<ip + 1>{});
+      const A sp = fa + fb, sm = fa - fb;
+      s1p = fma(A(p0), sp, s1p);
+      s1m = fma(A(p0), sm, s1m);
+      s2p = fma(A(p0 * p0), sp, s2p);
+      s2m = fma(A(p0 * p0), sm, s2m);
+    });
+    constexpr int vx = L::VX[first], vy = L::VY[first], vz = L::VZ[first];
+    constexpr double ir = L::INV_R, ir2 = L::INV_R2;
+    m.N0 += s1p;
+    m.T00 += s2p;
+    if constexpr (vx != 0) {
+      m.Nx = fma(A(vx * ir), s1m, m.Nx);
+      m.T0x = fma(A(vx * ir), s2m, m.T0x);
+      m.Txx = fma(A(vx * vx * ir2), s2p, m.Txx);
+    }
+    if constexpr (vy != 0) {
+      m.Ny = fma(A(vy * ir), s1m, m.Ny);
+      m.T0y = fma(A(vy * ir), s2m, m.T0y);
+      m.Tyy = fma(A(vy * vy * ir2), s2p, m.Tyy);
+    }
+    if constexpr (vz != 0) {
+      m.Nz = fma(A(vz * ir), s1m, m.Nz);
+      m.T0z = fma(A(vz * ir), s2m, m.T0z);
+    }
+    if constexpr (vx != 0 && vy != 0) m.Txy = fma(A(vx * vy * ir2), s2p, m.Txy);
+    if constexpr (vx != 0 && vz != 0) m.Txz = fma(A(vx * vz * ir2), s2p, m.Txz);
+    if constexpr (vy != 0 && vz != 0) m.Tyz = fma(A(vy * vz * ir2), s2p, m.Tyz);
+  });
+  // |v|^2 = R^2 for every velocity, so the spatial trace of T equals T^00.
+  m.Tzz = m.T00 - m.Txx - m.Tyy;
+  return m;
+}
+
+template <class A, class B>
+__device__ __forceinline__ Mom<B> convert(const Mom<A>& a) {
+  return Mom<B>{B(a.N0),  B(a.Nx),  B(a.Ny),  B(a.Nz),  B(a.T00), B(a.T0x), B(a.T0y),
+                B(a.T0z), B(a.Txx), B(a.Tyy), B(a.Tzz), B(a.Txy), B(a.Txz), B(a.Tyz)};
+}
+
+__device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+
+// ---------------------------------------------------------------------------------------------
+// Landau matching (Eq. (eigenproblem), Sec. II.D).  U is the timelike eigenvector of
+// T^a_b = T^{ac} eta_{cb}.  Shifted power iteration started from the Eckart vector N/|N|:
+//   V = T.(eta U),  rho = U.V,  W = V + (rho/3) U,  U <- W / |W|.
+// The shift rho/3 moves the spacelike eigenvalues -P_k to rho/3 - P_k, which vanish in local
+// equilibrium (eps = 3P), so the contraction factor is the relative pressure anisotropy instead
+// of P/eps = 1/3.  eps is the Rayleigh quotient U.V, n = U.N.
+// ---------------------------------------------------------------------------------------------
+template <class A>
+struct Landau {
+  A U0, Ux, Uy, Uz, eps, n;
+  bool ok;
+};
+
+template <class A, int MAXIT, bool EARLY>
+__device__ __forceinline__ Landau<A> landau(const Mom<A>& m) {
+  Landau<A> r;
+  r.ok = false;
+  const A NN = m.N0 * m.N0 - m.Nx * m.Nx - m.Ny * m.Ny - m.Nz * m.Nz;
+  if (!(NN > A(0)) || !(m.N0 > A(0))) return r;
+  A is = rsqrt_(NN);
+  A U0 = m.N0 * is, Ux = m.Nx * is, Uy = m.Ny * is, Uz = m.Nz * is;
+  const A tol = std::is_same<A, double>::value ? A(8e-16) : A(0);
+  for (int it = 0; it < MAXIT; ++it) {
+    const A V0 = m.T00 * U0 - m.T0x * Ux - m.T0y * Uy - m.T0z * Uz;
+    const A Vx = m.T0x * U0 - m.Txx * Ux - m.Txy * Uy - m.Txz * Uz;
+    const A Vy = m.T0y * U0 - m.Txy * Ux - m.Tyy * Uy - m.Tyz * Uz;
+    const A Vz = m.T0z * U0 - m.Txz * Ux - m.Tyz * Uy - m.Tzz * Uz;
+    const A s = (U0 * V0 - Ux * Vx - Uy * Vy - Uz * Vz) * A(1.0 / 3.0);
+    const A W0 = fma(s, U0, V0), Wx = fma(s, Ux, Vx), Wy = fma(s, Uy, Vy), Wz = fma(s, Uz, Vz);
+    const A WW = W0 * W0 - Wx * Wx - Wy * Wy - Wz * Wz;
+    if (!(WW > A(0)) || !(W0 > A(0))) return r;
+    const A iw = rsqrt_(WW);
+    const A n0 = W0 * iw, nx = Wx * iw, ny = Wy * iw, nz = Wz * iw;
+    if constexpr (EARLY) {
+      const A d = fmax(fmax(fabs(n0 - U0), fabs(nx - Ux)), fmax(fabs(ny - Uy), fabs(nz - Uz)));
+      U0 = n0; Ux = nx; Uy = ny; Uz = nz;
+      if (d <= tol * U0) break;
+    } else {
+      U0 = n0; Ux = nx; Uy = ny; Uz = nz;
+    }
+  }
+  const A V0 = m.T00 * U0 - m.T0x * Ux - m.T0y * Uy - m.T0z * Uz;
+  const A Vx = m.T0x * U0 - m.Txx * Ux - m.Txy * Uy - m.Txz * Uz;
+  const A Vy = m.T0y * U0 - m.Txy * Ux - m.Tyy * Uy - m.Tyz * Uz;
+  const A Vz = m.T0z * U0 - m.Txz * Ux - m.Tyz * Uy - m.Tzz * Uz;
+  r.eps = U0 * V0 - Ux * Vx - Uy * Vy - Uz * Vz;
+  r.n = U0 * m.N0 - Ux * m.Nx - Uy * m.Ny - Uz * m.Nz;
+  r.U0 = U0; r.Ux = Ux; r.Uy = Uy; r.Uz = Uz;
+  r.ok = (r.eps > A(0)) && (r.n > A(0)) && isfinite(r.eps) && isfinite(r.n);
+  return r;
+}
+
+// Landau matching in the step's arithmetic A.  Reduced-precision paths switch to double for cells
+// whose Eckart Lorentz factor exceeds gamma_thr (or always, if asked): the solve loses about
+// gamma^2 digits to cancellation in U.U = 1.
+template <class A>
+__device__ __forceinline__ Landau<A> landau_step(const Mom<A>& m, const StepParams& p) {
+  if constexpr (std::is_same<A, double>::value) {
+    return landau<double, 40, true>(m);
+  } else {
+    const float NN = m.N0 * m.N0 - m.Nx * m.Nx - m.Ny * m.Ny - m.Nz * m.Nz;
+    if (p.landau_fp64 || m.N0 * m.N0 > p.gamma_thr2 * NN) {
+      const Landau<double> d = landau<double, 40, true>(convert<A, double>(m));
+      return Landau<A>{(A)d.U0, (A)d.Ux, (A)d.Uy, (A)d.Uz, (A)d.eps, (A)d.n, d.ok};
+    }
+    return landau<float, 8, false>(m);
+  }
+}
+
+template <class A>
+__device__ __forceinline__ A tau_prime(A T, const StepParams& p) {
+  if (p.tau_fixed > 0.5) return A(p.tau_fixed);
+  const A Tt = p.tau_local ? T : A(p.T_ref);
+  return A(0.5) + A(p.tau_coef) / Tt;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Equilibrium in factored form.  The projection of the Maxwell-Juttner distribution onto the
+// polynomials of degree <= order depends on p only through p0 and s = p.U (rotational symmetry
+// about U), so f_i^eq = w_i E(p0_i, t_i) with s = p0 t, t = v.U/R, and, with x = T U0 - 1:
+//   order 3:  E = n/(12T) [c00 + p0 (c10 + c01 t) + p0^2 (c20 + c11 t + c02 t^2) + p0^3 (x + T t)^3]
+//   order 2:  E = n/(4T)  [c00 + p0 (c10 + c01 t) + p0^2 (x + T t)^2]
+// which is App. B's Eq. (eq:equi3rd) / (eq:equi2nd) regrouped.
+// ---------------------------------------------------------------------------------------------
+template <int ORDER, class A>
+struct EqCoef {
+  A c00, c10, c01, c20, c11, c02, x, T, pref;
+};
+
+template <int ORDER, class A>
+__device__ __forceinline__ EqCoef<ORDER, A> eq_coef(A n, A T, A U0) {
+  EqCoef<ORDER, A> c;
+  const A x = fma(T, U0, A(-1));
+  const A x2 = x * x, T2 = T * T;
+  c.x = x;
+  c.T = T;
+  if constexpr (ORDER == 3) {
+    const A pref = n / (A(12) * T);
+    c.pref = pref;
+    c.c00 = A(-6) * pref * (fma(x2, fma(A(8), x, A(4)), fma(A(4), x, A(-2))) + T2 * fma(A(-4), x, A(1)));
+    c.c10 = A(6) * pref * (fma(x2, fma(A(12), x, A(8)), fma(A(5), x, A(-1))) + T2 * fma(A(-6), x, A(1)));
+    c.c01 = A(6) * pref * T * (fma(A(12), x2, A(3)) - A(2) * T2);
+    c.c20 = A(-3) * pref * x * (fma(x, fma(A(6), x, A(3)), A(2)) - A(2) * T2);
+    c.c11 = A(-6) * pref * T * (fma(x, fma(A(6), x, A(1)), A(1)) - T2);
+    c.c02 = A(-3) * pref * T2 * fma(A(6), x, A(-1));
+  } else {
+    const A pref = n / (A(4) * T);
+    c.pref = pref;
+    c.c00 = A(2) * pref * (fma(A(4), x2, A(2)) - T2);
+    c.c10 = A(-2) * pref * (fma(x, fma(A(4), x, A(1)), A(1)) - T2);
+    c.c01 = A(-2) * pref * T * fma(A(4), x, A(-1));
+    c.c20 = c.c11 = c.c02 = A(0);
+  }
+  return c;
+}
+
+// Collision of one cell (Eq. (rlb:disc) right-hand side, delta t' = 1):
+//   f*_i = f_i + omega_i (w_i E_i - f_i),  omega_i = p_i.U / (tau' p0_i) = (U0 - t_i) / tau'.
+template <class L, class A, class Get, class Put>
+__device__ __forceinline__ void collide(const Landau<A>& lw, A T, A inv_tau, Get&& get, Put&& put) {
+  const EqCoef<L::ORDER, A> c = eq_coef<L::ORDER, A>(lw.n, T, lw.U0);
+  const A a = lw.U0 * inv_tau;
+  static_for<L::NDP>([&](auto K) {
+    constexpr int k = decltype(K)::value;
+    constexpr int first = L::DP_FIRST[k];
+    constexpr int np = L::DP_NPAIR[k];
+    constexpr int vx = L::VX[first], vy = L::VY[first], vz = L::VZ[first];
+    constexpr double ir = L::INV_R;
+    A t = A(0);
+    if constexpr (vx != 0) t = fma(A(vx * ir), lw.Ux, t);
+    if constexpr (vy != 0) t = fma(A(vy * ir), lw.Uy, t);
+    if constexpr (vz != 0) t = fma(A(vz * ir), lw.Uz, t);
+    // direction +v: t; mirror -v: -t
+    const A q1o = c.c01 * t;
+    const A q1p = c.c10 + q1o, q1m = c.c10 - q1o;
+    const A up = fma(c.T, t, c.x), um = fma(-c.T, t, c.x);
+    // qNp / qNm: coefficient of p0^N for direction +v / -v
+    A q2p, q2m, q3p, q3m;
+    if constexpr (L::ORDER == 3) {
+      const A q2e = fma(c.c02, t * t, c.c20), q2o = c.c11 * t;
+      q2p = q2e + q2o;
+      q2m = q2e - q2o;
+      q3p = c.pref * (up * up * up);
+      q3m = c.pref * (um * um * um);
+    } else {
+      q2p = c.pref * (up * up);
+      q2m = c.pref * (um * um);
+      q3p = q3m = A(0);
+    }
+    const A omp = fma(-t, inv_tau, a), omm = fma(t, inv_tau, a);
+    static_for<np>([&](auto J) {
+      constexpr int ip = first + 2 * decltype(J)::value;
+      constexpr double p0d = L::P0[L::LEV[ip]];
+      constexpr double wd = L::W[ip];
+      const A p0 = A(p0d), w = A(wd);
+      A Ep, Em;
+      if constexpr (L::ORDER == 3) {
+        Ep = fma(p0, fma(p0, fma(p0, q3p, q2p), q1p), c.c00);
+        Em = fma(p0, fma(p0, fma(p0, q3m, q2m), q1m), c.c00);
+      } else {
+        Ep = fma(p0, fma(p0, q2p, q1p), c.c00);
+        Em = fma(p0, fma(p0, q2m, q1m), c.c00);
+        (void)q3p;
+        (void)q3m;
+      }
+      const A fp = get(ic<ip>{}), fm = get(ic<ip + 1>{});
+      put(ic<ip>{}, fma(omp, fma(w, Ep, -fp), fp));
+      put(ic<ip + 1>{}, fma(omm, fma(w, Em, -fm), fm));
+    });
+  });
+}
+
+// ---------------------------------------------------------------------------------------------
+// the fused step kernel
+// ---------------------------------------------------------------------------------------------
+template <class L, class S, bool GENERAL>
+__global__ void __launch_bounds__(kStepThreads) k_step(const typename S::T* __restrict__ src,
+                                                       typename S::T* __restrict__ dst,
+                                                       const __grid_constant__ StepParams p,
+                                                       int* __restrict__ status) {
+  using A = typename S::A;
+  using ST = typename S::T;
+  const int gid = blockIdx.x * kStepThreads + threadIdx.x;
+  const bool valid = gid < p.cells;
+  const Cell cl = make_cell(valid ? gid : p.cells - 1, p);
+  // Warp-uniform choice: if every lane's stencil stays inside the lattice, pull with constant
+  // offsets; otherwise resolve periodic wrap / copy-out per population.
+  const bool fast = __all_sync(0xffffffffu, is_interior<L>(cl, p));
+  const ST* __restrict__ base = src + cl.c;
+
+  auto load = [&](auto I) -> A {
+    constexpr int i = decltype(I)::value;
+    if (fast) return S::template load<L, i>(base + p.off[i], p);
+    return S::template load<L, i>(src + pull_index<L, i, GENERAL>(cl, p), p);
+  };
+
+  A fk[S::kKeep ? L::Q : 1];
+  if constexpr (S::kKeep) {
+    static_for<L::Q>([&](auto I) { fk[decltype(I)::value] = load(I); });
+  }
+  auto get = [&](auto I) -> A {
+    if constexpr (S::kKeep) return fk[decltype(I)::value];
+    else return load(I);
+  };
+
+  const Mom<A> m = moments<L, A>(get);
+  const Landau<A> lw = landau_step<A>(m, p);
+  ST* __restrict__ out = dst + cl.c;
+  if (!lw.ok) {
+    // no Landau frame: record it and stream the populations without collision
+    if (valid) {
+      atomicAdd(&status[kStatusNonconv], 1);
+      static_for<L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        S::template store<L, i>(out + (long long)i * p.cells, get(I), p);
+      });
+    }
+    return;
+  }
+  const A T = lw.eps / (A(3) * lw.n);
+  const A inv_tau = A(1) / tau_prime<A>(T, p);
+  auto put = [&](auto I, A v) {
+    constexpr int i = decltype(I)::value;
+    if (valid) S::template store<L, i>(out + (long long)i * p.cells, v, p);
+  };
+  collide<L, A>(lw, T, inv_tau, get, put);
+}
+
+// ---------------------------------------------------------------------------------------------
+// fields and conserved densities of one time level (double arithmetic)
+//   PULL = true : the pre-collision populations pulled from the previous state
+//   PULL = false: the stored populations of each cell
+// fields[k][cell], k = n, eps, U0, U1, U2, U3; partial[block][5] = block sums of
+// N^0, T^00, T^0x, T^0y, T^0z, reduced by warp shuffles in a fixed order.
+// ---------------------------------------------------------------------------------------------
+template <class L, class S, bool PULL>
+__global__ void __launch_bounds__(kMomThreads) k_fields(const typename S::T* __restrict__ src,
+                                                        const __grid_constant__ StepParams p,
+                                                        double* __restrict__ fields,
+                                                        double* __restrict__ partial,
+                                                        int* __restrict__ status) {
+  const int gid = blockIdx.x * kMomThreads + threadIdx.x;
+  const bool valid = gid < p.cells;
+  const Cell cl = make_cell(valid ? gid : p.cells - 1, p);
+  auto get = [&](auto I) -> double {
+    constexpr int i = decltype(I)::value;
+    const long long idx = PULL ? pull_index<L, i, true>(cl, p) : (long long)i * p.cells + cl.c;
+    return S::template to_f64<L, i>(src[idx], p);
+  };
+  const Mom<double> m = moments<L, double>(get);
+  const Landau<double> lw = landau<double, 200, true>(m);
+  if (valid) {
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    fields[0 * (long long)p.cells + cl.c] = lw.ok ? lw.n : nan;
+    fields[1 * (long long)p.cells + cl.c] = lw.ok ? lw.eps : nan;
+    fields[2 * (long long)p.cells + cl.c] = lw.ok ? lw.U0 : nan;
+    fields[3 * (long long)p.cells + cl.c] = lw.ok ? lw.Ux : nan;
+    fields[4 * (long long)p.cells + cl.c] = lw.ok ? lw.Uy : nan;
+    fields[5 * (long long)p.cells + cl.c] = lw.ok ? lw.Uz : nan;
+    if (!lw.ok) atomicAdd(&status[kStatusNonconv], 1);
+  }
+  double d[5] = {valid ? m.N0 : 0.0, valid ? m.T00 : 0.0, valid ? m.T0x : 0.0, valid ? m.T0y : 0.0,
+                 valid ? m.T0z : 0.0};
+#pragma unroll
+  for (int k = 0; k < 5; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d[k] += __shfl_down_sync(0xffffffffu, d[k], o);
+  __shared__ double ws[kMomThreads / 32][5];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < 5; ++k) ws[warp][k] = d[k];
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kMomThreads / 32; ++w) s += ws[w][threadIdx.x];
+    partial[(long long)blockIdx.x * 5 + threadIdx.x] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// initial state f_i = f_i^eq(n, T, u) (double arithmetic), and population format conversion
+// ---------------------------------------------------------------------------------------------
+template <class L, class S>
+__global__ void __launch_bounds__(128) k_init(const double* __restrict__ n, const double* __restrict__ Tf,
+                                              const double* __restrict__ u, typename S::T* __restrict__ dst,
+                                              const __grid_constant__ StepParams p, int* __restrict__ status) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.cells) return;
+  const long long cells = p.cells;
+  const double ux = u[c], uy = u[cells + c], uz = u[2 * cells + c];
+  const double u2 = ux * ux + uy * uy + uz * uz;
+  const double nn = n[c], T = Tf[c];
+  if (!(u2 < 1.0) || !(T > 0.0) || !(nn > 0.0)) {
+    atomicAdd(&status[kStatusBadInit], 1);
+    return;
+  }
+  const double g = rsqrt(1.0 - u2);
+  const double Ux = g * ux, Uy = g * uy, Uz = g * uz;
+  const EqCoef<L::ORDER, double> cf = eq_coef<L::ORDER, double>(nn, T, g);
+  static_for<L::NDP>([&](auto K) {
+    constexpr int k = decltype(K)::value;
+    constexpr int first = L::DP_FIRST[k];
+    constexpr int np = L::DP_NPAIR[k];
+    constexpr int vx = L::VX[first], vy = L::VY[first], vz = L::VZ[first];
+    const double t = (vx * Ux + vy * Uy + vz * Uz) * L::INV_R;
+    static_for<np>([&](auto J) {
+      constexpr int ip = first + 2 * decltype(J)::value;
+      constexpr double p0 = L::P0[L::LEV[ip]];
+      constexpr double w = L::W[ip];
+      for (int sgn = 0; sgn < 2; ++sgn) {
+        const double tt = sgn ? -t : t;
+        const double u_ = fma(cf.T, tt, cf.x);
+        double E;
+        if constexpr (L::ORDER == 3)
+          E = cf.c00 + p0 * (cf.c10 + cf.c01 * tt + p0 * (cf.c20 + cf.c11 * tt + cf.c02 * tt * tt +
+                                                          p0 * cf.pref * u_ * u_ * u_));
+        else
+          E = cf.c00 + p0 * (cf.c10 + cf.c01 * tt + p0 * cf.pref * u_ * u_);
+        if (sgn == 0)
+          S::template store<L, ip>(dst + (long long)ip * cells + c, (typename S::A)(w * E), p);
+        else
+          S::template store<L, ip + 1>(dst + (long long)(ip + 1) * cells + c, (typename S::A)(w * E), p);
+      }
+    });
+  });
+}
+
+// double[q][cells] <-> storage, for populations [i0, i1) (in-range cells only)
+template <class L, class S, bool TO_F64>
+__global__ void __launch_bounds__(128) k_convert(typename S::T* __restrict__ pop, double* __restrict__ dbl,
+                                                 long long dbl_plane_offset, int i0, int i1,
+                                                 const __grid_constant__ StepParams p) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.cells) return;
+  const long long cells = p.cells;
+  static_for<L::Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if (i < i0 || i >= i1) return;
+    const long long di = (long long)(i - i0) * cells + c + dbl_plane_offset;
+    if constexpr (TO_F64) dbl[di] = S::template to_f64<L, i>(pop[(long long)i * cells + c], p);
+    else pop[(long long)i * cells + c] = S::template from_f64<L, i>(dbl[di], p);
+  });
+}
+
+}  // namespace rlb

@@ -1,0 +1,28 @@
+// Host-side launchers, one set per (order, storage) instantiation (rlb_inst.cu is compiled once
+// per pair so that the translation units build in parallel).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace rlb {
+struct StepParams;
+
+struct Launchers {
+  cudaError_t (*step)(const void* src, void* dst, const StepParams& p, int* status, bool general, cudaStream_t s);
+  cudaError_t (*fields)(const void* src, const StepParams& p, double* fields, double* partial, int* status, bool pull,
+                        cudaStream_t s);
+  cudaError_t (*init)(const double* n, const double* T, const double* u, void* dst, const StepParams& p, int* status,
+                      cudaStream_t s);
+  cudaError_t (*convert)(void* pop, double* dbl, int i0, int i1, bool to_f64, const StepParams& p, cudaStream_t s);
+};
+
+#define RLB_DECLARE_LAUNCHERS(ORDER, STORAGE) extern const Launchers launchers_o##ORDER##_s##STORAGE;
+RLB_DECLARE_LAUNCHERS(3, 0)
+RLB_DECLARE_LAUNCHERS(3, 1)
+RLB_DECLARE_LAUNCHERS(3, 2)
+RLB_DECLARE_LAUNCHERS(2, 0)
+RLB_DECLARE_LAUNCHERS(2, 1)
+RLB_DECLARE_LAUNCHERS(2, 2)
+#undef RLB_DECLARE_LAUNCHERS
+
+cudaError_t launch_reduce_partials(const double* partial, int nblocks, double* totals, cudaStream_t s);
+}  // namespace rlb

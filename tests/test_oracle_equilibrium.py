@@ -22,22 +22,57 @@ def test_rest_value(order):
     """At T = 1 and U = (1, 0, 0, 0) both appendix formulas reduce to f_i^eq = n w_i / 2, which is
     exp(-p0) n / (8 pi) divided by the weight exp(-p0) / (4 pi) (Sec. II.B with A = 1/(4 pi))."""
     lat = oracle.read_lattice(order)
-    f = oracle.equilibrium_cell(lat, 0.7, 1.0, [1.0, 0.0, 0.0, 0.0])
-    assert np.allclose(f, 0.35 * lat.w, rtol=1e-14, atol=0)
+    # projection route: round-off through basis values up to ~1e3 at p0 ~ 11
+    assert np.allclose(oracle.equilibrium_cell(lat, 0.7, 1.0, [1.0, 0.0, 0.0, 0.0]), 0.35 * lat.w, rtol=1e-13, atol=0)
+    assert np.allclose(oracle.equilibrium_appendix_cell(lat, 0.7, 1.0, [1.0, 0.0, 0.0, 0.0]), 0.35 * lat.w,
+                       rtol=1e-14, atol=0)
 
 
 @pytest.mark.parametrize("order", [3, 2])
 def test_appendix_equals_gram_schmidt_projection(order):
     """The printed explicit equilibrium (Eq. (eq:equi3rd) / (eq:equi2nd)) equals the projection
-    sum_k a_k J_k built independently by Gram-Schmidt (Eqs. (eq:expanded), (coeff))."""
+    sum_k a_k J_k built independently by Gram-Schmidt (Eqs. (eq:expanded), (coeff)).  The explicit
+    form, a polynomial in powers of p with terms up to ~1e4 times the result at T ~ 2, p0 ~ 11,
+    carries rounding of order 1e-12 of the population scale."""
     lat = oracle.read_lattice(order)
     rng = np.random.default_rng(11 + order)
     for _ in range(20):
         n, T, U = random_state(rng, vmax=0.9)
-        a = oracle.equilibrium_cell(lat, n, T, U)
+        a = oracle.equilibrium_appendix_cell(lat, n, T, U)
         b = pj.equilibrium(lat, n, T, U)
         scale = np.maximum(np.abs(b), n * lat.w / 2)
         assert np.max(np.abs(a - b) / scale) < 1e-11
+
+
+@pytest.mark.parametrize("order", [3, 2])
+def test_oracle_projection_matches_exact_rational_route(order):
+    """The C oracle's sum_k a_k J_k(p_i) (basis table from exact Gram-Schmidt, evaluated in long
+    double) equals the numpy route over the same exact basis, and both sit within 1e-13 of the
+    population scale of a 50-digit evaluation of the same projection."""
+    import mpmath as mp
+    lat = oracle.read_lattice(order)
+    rng = np.random.default_rng(17 + order)
+    M, basis, norms = pj.orthogonal_basis(order)
+    mp.mp.dps = 50
+    for _ in range(6):
+        n, T, U = random_state(rng, vmax=0.8)
+        a = oracle.equilibrium_cell(lat, n, T, U)
+        b = pj.equilibrium(lat, n, T, U)
+        scale = np.maximum(np.abs(b), n * lat.w / 2)
+        assert np.max(np.abs(a - b) / scale) < 1e-13
+        # 50-digit reference for a few populations
+        s_, N_, T_, P_ = pj.mj_moments(n, T, U)
+        bj = [mp.mpf(float(pj._monomial_moment(m, s_, N_, T_, P_))) for m in M]
+        for i in (0, lat.q // 2, lat.q - 1, int(np.argmax(lat.p0))):
+            p = [mp.mpf(float(lat.p0[i]))] + [mp.mpf(float(lat.p0[i])) * int(c) / mp.sqrt(lat.R2) for c in lat.v[i]]
+            mv = [p[0] ** e0 * p[1] ** x * p[2] ** y * p[3] ** z for e0, (x, y, z) in M]
+            val = 0
+            for P, nn in zip(basis, norms):
+                ak = sum(mp.mpf(c.numerator) / c.denominator * bj[j] for j, c in enumerate(P) if c) / (
+                    mp.mpf(nn.numerator) / nn.denominator)
+                val += ak * sum(mp.mpf(c.numerator) / c.denominator * mv[j] for j, c in enumerate(P) if c)
+            exact = float(lat.w[i] * val)
+            assert abs(a[i] - exact) < 1e-13 * scale[i]
 
 
 def test_projection_off_lattice_momenta():
