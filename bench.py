@@ -40,7 +40,10 @@ N_LATTICE = 256
 ORDER = 3
 Q = 128
 ETA_S = 0.1
-WORKLOAD = "random-field 256^3 periodic, third-order RLB (Q=128, R^2=41), FP32 storage, eta/s=0.1"
+DENSITY = "uniform"
+SIGMA_LNT = 0.2
+WORKLOAD = ("random-field %d^3 periodic, third-order RLB (Q=128, R^2=41), FP32 storage, eta/s=0.1, "
+            "max|v|=0.6, log-normal T (sigma 0.2, mean 1), uniform n")
 
 
 def measured_peaks():
@@ -118,34 +121,39 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_baseline(budget_s=12.0):
-    """The FP64 oracle, as it stands, on one host core: 32^3 periodic lattice of the same
-    random-field generator, stepping until about budget_s seconds are spent."""
+def cpu_baseline(n, T, u, budget_s=12.0, planes=2):
+    """The FP64 oracle, as it stands, on one host core, timed on a bounded sample of the workload:
+    the first ``planes`` z-planes of the same initial fields as a periodic slab, stepped until
+    about budget_s seconds are spent."""
     import oracle
     lat = oracle.read_lattice(ORDER)
-    n_side = 32
-    n, T, u = gen.smooth_random_fields((n_side,) * 3, seed=1, vmax=0.6, sigma_lnT=0.2)
-    o = oracle.OracleRLB(lat, n_side, n_side, n_side, eta_over_s=ETA_S)
-    o.init(n, T, u)
+    ns, Ts, us = n[:planes].copy(), T[:planes].copy(), u[:, :planes].copy()
+    nz, ny, nx = ns.shape
+    o = oracle.OracleRLB(lat, nx, ny, nz, eta_over_s=ETA_S)
+    o.init(ns, Ts, us)
     t0 = time.perf_counter()
     steps = 0
     while time.perf_counter() - t0 < budget_s:
         o.step(1)
         steps += 1
     dt = time.perf_counter() - t0
-    return {"value": n_side ** 3 * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": "%d steps of a %d^3 periodic lattice of the same random-field workload (serial FP64 C "
-                      "oracle, %.1f s)" % (steps, n_side, n_side, dt)}
+    cells = nx * ny * nz
+    return {"value": cells * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "%d steps of the first %d z-planes of the %dx%dx%d workload as a periodic %dx%dx%d slab "
+                      "(%d cells; serial FP64 C oracle, %.1f s)" % (steps, planes, nx, ny, nx, nx, ny, nz, cells, dt)}
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    cb = cpu_baseline(budget_s=max(3.0, 4.0 * args.steps / max(args.steps, 1)))
+    N = args.n
+    n, T, u = gen.smooth_random_fields((N, N, N), seed=1, vmax=0.6, sigma_lnT=args.sigma, density=args.density)
+    cb = cpu_baseline(n, T, u, budget_s=max(10.0, min(60.0, 0.1 * args.steps)))
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD.replace("FP32 storage", "FP64 CPU oracle"), "sample": cb["sample"]},
+            "config": {"workload": (WORKLOAD % N).replace("FP32 storage", "FP64 CPU oracle"), "sample": cb["sample"],
+                       "sigma_lnT": args.sigma, "density": args.density},
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -161,6 +169,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--density", default=DENSITY, choices=["uniform", "cube"],
+                    help="initial density: uniform n = 1, or n = T^3")
+    ap.add_argument("--sigma", type=float, default=SIGMA_LNT, help="std of ln T")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -175,7 +186,7 @@ def main():
     N = args.n
     shape = (N, N, N)
     cells = N ** 3
-    n, T, u = gen.smooth_random_fields(shape, seed=1 + rank, vmax=0.6, sigma_lnT=0.2)
+    n, T, u = gen.smooth_random_fields(shape, seed=1 + rank, vmax=0.6, sigma_lnT=args.sigma, density=args.density)
 
     def barrier():
         if world > 1:
@@ -193,6 +204,7 @@ def main():
     # ---- device-resident throughput (the headline value) ------------------------------------
     g = RLB(shape, order=ORDER, storage="f32", eta_over_s=ETA_S, stream=stream)
     g.init(n, T, u)
+    variant, variant_ms = g.autotune(reps=3)
     g.step(args.warmup)
     g.sync()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -211,7 +223,7 @@ def main():
     launches = g.kernel_launches - launches0
     ms_total = e0.elapsed_time(e1)
     ms_total_max = max_over_ranks(ms_total)
-    g.sync()
+    g.sync()  # raises if any cell lost its Landau frame: a broken simulation is not a measurement
     value = world * cells * args.steps / (ms_total_max * 1e-3) / 1e6
     per_launch_s = ms_total * 1e-3 / launches
     algo_bytes = cells * Q * 2 * 4
@@ -252,7 +264,7 @@ def main():
         on, oe, oU = (torch.empty(shape, dtype=torch.float64).pin_memory(),
                       torch.empty(shape, dtype=torch.float64).pin_memory(),
                       torch.empty((4,) + shape, dtype=torch.float64).pin_memory())
-        ge = RLB(shape, order=ORDER, storage="f32", eta_over_s=ETA_S, stream=stream)
+        ge = RLB(shape, order=ORDER, storage="f32", eta_over_s=ETA_S, stream=stream, step_variant=variant)
         ptr = lambda t: t.numpy()
         ge.init(ptr(hn), ptr(hT), ptr(hu))
         ge.step(args.warmup)
@@ -273,23 +285,26 @@ def main():
 
     if rank != 0:
         return
-    cb = None if args.no_cpu_baseline else cpu_baseline()
+    cb = None if args.no_cpu_baseline else cpu_baseline(n, T, u)
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "lattice": [N, N, N], "order": ORDER, "q": Q, "storage": "f32",
-                   "eta_over_s": ETA_S, "boundary": "periodic", "parallelism": "replicas" if world > 1 else "single",
+        "config": {"workload": WORKLOAD % N, "lattice": [N, N, N], "order": ORDER, "q": Q, "storage": "f32",
+                   "eta_over_s": ETA_S, "max_v": 0.6, "sigma_lnT": args.sigma, "density": args.density, "boundary": "periodic", "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2: two population buffers of %.1f GB" % (cells * Q * 4 / 1e9),
                    "baseline_metric": BASELINE_METRIC},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                      "peak_source": peak_src, "algorithmic_bytes_per_launch": algo_bytes,
-                     "kernel": "k_step<Quad3, StoreF32>", "launch_ms": per_launch_s * 1e3},
+                     "kernel": "k_step<Quad3, StoreF32, variant %d>" % variant, "launch_ms": per_launch_s * 1e3},
         "cpu_baseline": cb,
         "e2e": e2e,
         "fp64_plain": fp64,
         "gpu_launches": launches,
+        "autotune": {"variant": variant, "ms_per_step": variant_ms,
+                     "variants": ["scalar, 2 blocks/SM", "paired, 2 blocks/SM", "scalar, 3 blocks/SM",
+                                  "paired, 3 blocks/SM"]},
         "clocks": clk.summary(),
         "wall_s_timed_region": t_wall,
     }

@@ -78,6 +78,8 @@ typedef struct {
   double gamma_thr;   /* RLB_F32 / RLB_F16DEV only: cells whose Eckart Lorentz factor exceeds this
                          are solved in double (default 2.0) */
   double n_ref;       /* RLB_F16DEV only: reference density of the stored deviation (default 1.0) */
+  int step_variant;   /* float storage only: -1 = library default, or force a step-kernel variant
+                         0..3 (see rlb_autotune); ignored for RLB_F64 */
   void* stream;       /* cudaStream_t to enqueue on; NULL = the default stream */
   /* Optional quadrature (Sec. II.C, App. A).  When q > 0 these arrays are compared with the
    * quadrature compiled into the library for this order and must match exactly (RLB_EINVAL
@@ -133,6 +135,16 @@ rlb_status rlb_get_populations(rlb_ctx* ctx, double* f, int on_device);
  * and treat them as the initial state: the step counter is reset to 0 and rlb_moments reports
  * their own fields.  Errors: RLB_EINVAL, RLB_ECUDA. */
 rlb_status rlb_set_populations(rlb_ctx* ctx, const double* f, int on_device);
+
+/* Autotuner: time every step-kernel variant of this context (for float storage: scalar or paired
+ * float arithmetic, 2 or 3 resident blocks per SM) on the context's own lattice
+ * and keep the fastest for later rlb_step calls.  Each variant repeats one step from the current
+ * populations into the spare buffer `reps` times, so the state does not change; this is allowed
+ * only before the first step after rlb_init / rlb_set_populations (RLB_ESTATE otherwise).
+ * *variant (may be NULL) receives the choice; ms[4] (may be NULL) the measured milliseconds per
+ * step of each variant (0 where a variant does not exist).  Synchronises the stream.
+ * Errors: RLB_EINVAL (reps < 1), RLB_ESTATE, RLB_ECUDA. */
+rlb_status rlb_autotune(rlb_ctx* ctx, int reps, int* variant, double ms[4]);
 
 /* Number of time steps taken since rlb_init / rlb_set_populations (-1 for NULL). */
 long rlb_steps_done(const rlb_ctx* ctx);

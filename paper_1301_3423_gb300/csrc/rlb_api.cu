@@ -58,6 +58,7 @@ struct rlb_ctx {
   int* status = nullptr;      // kStatusWords
   int fblocks = 0;
   const Launchers* launch = nullptr;
+  int variant = 0;            // step-kernel variant (float storage)
   std::string err;
 };
 
@@ -95,6 +96,7 @@ extern "C" void rlb_default_params(rlb_params* p) {
   p->landau_fp64 = 0;
   p->gamma_thr = 2.0;
   p->n_ref = 1.0;
+  p->step_variant = -1;
 }
 
 extern "C" rlb_status rlb_quadrature(int order, int* q, const int** vel, const int** level, const double** p0,
@@ -127,6 +129,7 @@ static std::string validate(const rlb_params* p) {
   }
   if (!(p->gamma_thr >= 1.0)) return "gamma_thr must be >= 1";
   if (p->storage == RLB_F16DEV && !(p->n_ref > 0)) return "n_ref must be > 0";
+  if (p->step_variant < -1 || p->step_variant > 3) return "step_variant must be -1 or 0..3";
   if (p->q > 0) {
     int q;
     const int *vel, *lev;
@@ -202,6 +205,8 @@ extern "C" rlb_status rlb_create(const rlb_params* p, rlb_ctx** out) {
   static const Launchers* const table[2][3] = {{&launchers_o2_s0, &launchers_o2_s1, &launchers_o2_s2},
                                                {&launchers_o3_s0, &launchers_o3_s1, &launchers_o3_s2}};
   c->launch = table[p->order == 3 ? 1 : 0][p->storage];
+  c->variant = (p->step_variant >= 0 && p->step_variant < c->launch->step_variants) ? p->step_variant
+                                                                                      : kDefaultStepVariant;
   if (p->order == 3) {
     fill_offsets<Quad3>(sp);
     c->general_wrap = needs_general_wrap<Quad3>(*p);
@@ -299,15 +304,55 @@ extern "C" rlb_status rlb_step(rlb_ctx* c, long nsteps) {
   if (!c) return RLB_EINVAL;
   if (nsteps < 0) return fail(c, RLB_EINVAL, "nsteps < 0");
   for (long s = 0; s < nsteps; ++s) {
-    rlb_status st = check_launch(
-        c, c->launch->step(c->buf[c->cur], c->buf[1 - c->cur], c->sp, c->status, c->general_wrap, c->stream),
-        "step kernel");
+    rlb_status st = check_launch(c,
+                                 c->launch->step(c->buf[c->cur], c->buf[1 - c->cur], c->sp, c->status,
+                                                 c->general_wrap, c->variant, c->stream),
+                                 "step kernel");
     if (st != RLB_OK) return st;
     c->cur = 1 - c->cur;
     c->have_prev = true;
     ++c->steps;
   }
   return RLB_OK;
+}
+
+extern "C" rlb_status rlb_autotune(rlb_ctx* c, int reps, int* variant, double ms[4]) {
+  if (!c) return RLB_EINVAL;
+  if (reps < 1) return fail(c, RLB_EINVAL, "rlb_autotune: reps < 1");
+  if (c->have_prev) return fail(c, RLB_ESTATE, "rlb_autotune: only before the first step after init");
+  cudaEvent_t e0, e1;
+  RLB_CUDA(c, cudaEventCreate(&e0));
+  RLB_CUDA(c, cudaEventCreate(&e1));
+  double best = 1e300;
+  int choice = c->variant;
+  double t[4] = {0, 0, 0, 0};
+  for (int v = 0; v < c->launch->step_variants; ++v) {
+    // warm-up launch, then the timed repetitions; every launch recomputes the same next state
+    for (int r = 0; r <= reps; ++r) {
+      if (r == 1) RLB_CUDA(c, cudaEventRecord(e0, c->stream));
+      rlb_status st = check_launch(c,
+                                   c->launch->step(c->buf[c->cur], c->buf[1 - c->cur], c->sp, c->status,
+                                                   c->general_wrap, v, c->stream),
+                                   "step kernel");
+      if (st != RLB_OK) return st;
+    }
+    RLB_CUDA(c, cudaEventRecord(e1, c->stream));
+    RLB_CUDA(c, cudaEventSynchronize(e1));
+    float msv = 0.f;
+    RLB_CUDA(c, cudaEventElapsedTime(&msv, e0, e1));
+    t[v] = msv / reps;
+    if (t[v] < best) {
+      best = t[v];
+      choice = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->variant = choice;
+  if (variant) *variant = choice;
+  if (ms)
+    for (int v = 0; v < 4; ++v) ms[v] = t[v];
+  return read_status(c);
 }
 
 extern "C" rlb_status rlb_moments(rlb_ctx* c, double* n, double* eps, double* U, double totals[5], int on_device) {

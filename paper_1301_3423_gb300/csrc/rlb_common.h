@@ -6,6 +6,7 @@ namespace rlb {
 constexpr int kStepThreads = 128;    // threads per block of the step kernel (one cell each)
 constexpr int kMomThreads = 128;     // threads per block of the fields kernel
 constexpr int kReduceThreads = 256;  // threads of the single-block second reduction pass
+constexpr int kDefaultStepVariant = 0;  // step-kernel variant before autotuning (float storage)
 
 // ---------------------------------------------------------------------------------------------
 // launch parameters

@@ -27,12 +27,29 @@ using S = StoreF16Dev;
 #endif
 using T = typename S::T;
 
-cudaError_t step(const void* src, void* dst, const StepParams& p, int* status, bool general, cudaStream_t s) {
+constexpr bool kFloat = std::is_same<typename S::A, float>::value;
+
+template <int V>
+void launch_step(const void* src, void* dst, const StepParams& p, int* status, bool general, cudaStream_t s) {
   const int blocks = (p.cells + kStepThreads - 1) / kStepThreads;
   if (general)
-    k_step<L, S, true><<<blocks, kStepThreads, 0, s>>>((const T*)src, (T*)dst, p, status);
+    k_step<L, S, true, V><<<blocks, kStepThreads, 0, s>>>((const T*)src, (T*)dst, p, status);
   else
-    k_step<L, S, false><<<blocks, kStepThreads, 0, s>>>((const T*)src, (T*)dst, p, status);
+    k_step<L, S, false, V><<<blocks, kStepThreads, 0, s>>>((const T*)src, (T*)dst, p, status);
+}
+
+cudaError_t step(const void* src, void* dst, const StepParams& p, int* status, bool general, int variant,
+                 cudaStream_t s) {
+  if constexpr (kFloat) {
+    switch (variant) {
+      case kRegScalar: launch_step<kRegScalar>(src, dst, p, status, general, s); break;
+      case kRegPacked: launch_step<kRegPacked>(src, dst, p, status, general, s); break;
+      case kRegScalar3: launch_step<kRegScalar3>(src, dst, p, status, general, s); break;
+      default: launch_step<kRegPacked3>(src, dst, p, status, general, s); break;
+    }
+  } else {
+    launch_step<kRegScalar>(src, dst, p, status, general, s);
+  }
   return cudaGetLastError();
 }
 
@@ -66,7 +83,8 @@ cudaError_t convert_pops(void* pop, double* dbl, int i0, int i1, bool to_f64, co
 
 #define RLB_CAT_(a, b, c, d) a##b##c##d
 #define RLB_NAME(o, s) RLB_CAT_(launchers_o, o, _s, s)
-extern const Launchers RLB_NAME(RLB_INST_ORDER, RLB_INST_STORAGE) = {step, fields, init, convert_pops};
+extern const Launchers RLB_NAME(RLB_INST_ORDER, RLB_INST_STORAGE) = {step, fields, init, convert_pops,
+                                                                  kFloat ? (int)kNumVariants : 1};
 
 #if RLB_INST_ORDER == 3 && RLB_INST_STORAGE == 0
 // Second pass of the conserved-density sums: one block adds the per-block partials in a fixed

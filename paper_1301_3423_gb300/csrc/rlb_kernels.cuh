@@ -388,15 +388,154 @@ __device__ __forceinline__ void collide(const Landau<A>& lw, A T, A inv_tau, Get
 }
 
 // ---------------------------------------------------------------------------------------------
+// Float arithmetic in mirror pairs.  Populations i (direction +v) and i + 1 (direction -v) share
+// energy and weight, so their work is one float2 operation (sm_100+ paired FP32 FMA):
+// moments accumulate per sign with sign-symmetric constants, and the equilibrium and collision of
+// the pair are evaluated together with t2 = (t, -t).
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+template <class L, class Get2>
+__device__ __forceinline__ Mom<float> moments_f2(Get2&& get2) {
+  const float2 z = f2(0.f, 0.f);
+  float2 N0 = z, Nx = z, Ny = z, Nz = z, T00 = z, T0x = z, T0y = z, T0z = z, Txx = z, Tyy = z, Txy = z, Txz = z, Tyz = z;
+  static_for<L::NDP>([&](auto K) {
+    constexpr int k = decltype(K)::value;
+    constexpr int first = L::DP_FIRST[k];
+    constexpr int np = L::DP_NPAIR[k];
+    float2 S1 = z, S2 = z;  // (sum over energies for +v, for -v)
+    static_for<np>([&](auto J) {
+      constexpr int ip = first + 2 * decltype(J)::value;
+      constexpr float p0 = (float)L::P0[L::LEV[ip]];
+      constexpr float p02 = (float)(L::P0[L::LEV[ip]] * L::P0[L::LEV[ip]]);
+      const float2 f = get2(ic<ip>{});
+      S1 = ffma2(f2(p0, p0), f, S1);
+      S2 = ffma2(f2(p02, p02), f, S2);
+    });
+    constexpr int vx = L::VX[first], vy = L::VY[first], vz = L::VZ[first];
+    constexpr double ir = L::INV_R, ir2 = L::INV_R2;
+    N0 = fadd2(N0, S1);
+    T00 = fadd2(T00, S2);
+    if constexpr (vx != 0) {
+      constexpr float c = (float)(vx * ir);
+      constexpr float cc = (float)(vx * vx * ir2);
+      Nx = ffma2(f2(c, -c), S1, Nx);
+      T0x = ffma2(f2(c, -c), S2, T0x);
+      Txx = ffma2(f2(cc, cc), S2, Txx);
+    }
+    if constexpr (vy != 0) {
+      constexpr float c = (float)(vy * ir);
+      constexpr float cc = (float)(vy * vy * ir2);
+      Ny = ffma2(f2(c, -c), S1, Ny);
+      T0y = ffma2(f2(c, -c), S2, T0y);
+      Tyy = ffma2(f2(cc, cc), S2, Tyy);
+    }
+    if constexpr (vz != 0) {
+      constexpr float c = (float)(vz * ir);
+      Nz = ffma2(f2(c, -c), S1, Nz);
+      T0z = ffma2(f2(c, -c), S2, T0z);
+    }
+    if constexpr (vx != 0 && vy != 0) {
+      constexpr float cc = (float)(vx * vy * ir2);
+      Txy = ffma2(f2(cc, cc), S2, Txy);
+    }
+    if constexpr (vx != 0 && vz != 0) {
+      constexpr float cc = (float)(vx * vz * ir2);
+      Txz = ffma2(f2(cc, cc), S2, Txz);
+    }
+    if constexpr (vy != 0 && vz != 0) {
+      constexpr float cc = (float)(vy * vz * ir2);
+      Tyz = ffma2(f2(cc, cc), S2, Tyz);
+    }
+  });
+  Mom<float> m;
+  m.N0 = N0.x + N0.y;
+  m.Nx = Nx.x + Nx.y;
+  m.Ny = Ny.x + Ny.y;
+  m.Nz = Nz.x + Nz.y;
+  m.T00 = T00.x + T00.y;
+  m.T0x = T0x.x + T0x.y;
+  m.T0y = T0y.x + T0y.y;
+  m.T0z = T0z.x + T0z.y;
+  m.Txx = Txx.x + Txx.y;
+  m.Tyy = Tyy.x + Tyy.y;
+  m.Txy = Txy.x + Txy.y;
+  m.Txz = Txz.x + Txz.y;
+  m.Tyz = Tyz.x + Tyz.y;
+  m.Tzz = m.T00 - m.Txx - m.Tyy;
+  return m;
+}
+
+template <class L, class Get2, class Put2>
+__device__ __forceinline__ void collide_f2(const Landau<float>& lw, float T, float inv_tau, Get2&& get2, Put2&& put2) {
+  const EqCoef<L::ORDER, float> c = eq_coef<L::ORDER, float>(lw.n, T, lw.U0);
+  const float a = lw.U0 * inv_tau;
+  const float2 Tp = f2(c.T, c.T), xp = f2(c.x, c.x), prefp = f2(c.pref, c.pref);
+  const float2 c00p = f2(c.c00, c.c00), c10p = f2(c.c10, c.c10), c01p = f2(c.c01, c.c01);
+  const float2 c20p = f2(c.c20, c.c20), c11p = f2(c.c11, c.c11), c02p = f2(c.c02, c.c02);
+  const float2 Uxp = f2(lw.Ux, lw.Ux), Uyp = f2(lw.Uy, lw.Uy), Uzp = f2(lw.Uz, lw.Uz);
+  const float2 itp = f2(inv_tau, inv_tau), nap = f2(-a, -a);
+  static_for<L::NDP>([&](auto K) {
+    constexpr int k = decltype(K)::value;
+    constexpr int first = L::DP_FIRST[k];
+    constexpr int np = L::DP_NPAIR[k];
+    constexpr int vx = L::VX[first], vy = L::VY[first], vz = L::VZ[first];
+    constexpr double ir = L::INV_R;
+    float2 tt = f2(0.f, 0.f);  // (t, -t), t = v.U / R
+    if constexpr (vx != 0) tt = ffma2(f2((float)(vx * ir), (float)(-vx * ir)), Uxp, tt);
+    if constexpr (vy != 0) tt = ffma2(f2((float)(vy * ir), (float)(-vy * ir)), Uyp, tt);
+    if constexpr (vz != 0) tt = ffma2(f2((float)(vz * ir), (float)(-vz * ir)), Uzp, tt);
+    const float2 up = ffma2(Tp, tt, xp);    // x + T t
+    const float2 q1 = ffma2(c01p, tt, c10p);
+    float2 q2, q3;
+    if constexpr (L::ORDER == 3) {
+      const float2 e2 = ffma2(c02p, fmul2(tt, tt), c20p);
+      q2 = ffma2(c11p, tt, e2);
+      q3 = fmul2(prefp, fmul2(fmul2(up, up), up));
+    } else {
+      q2 = fmul2(prefp, fmul2(up, up));
+      q3 = f2(0.f, 0.f);
+    }
+    const float2 nom = ffma2(itp, tt, nap);  // -(U0 - t) / tau' for +v, -(U0 + t) / tau' for -v
+    static_for<np>([&](auto J) {
+      constexpr int ip = first + 2 * decltype(J)::value;
+      constexpr float p0 = (float)L::P0[L::LEV[ip]];
+      constexpr float nw = (float)(-L::W[ip]);
+      const float2 p0p = f2(p0, p0);
+      float2 E;
+      if constexpr (L::ORDER == 3)
+        E = ffma2(p0p, ffma2(p0p, ffma2(p0p, q3, q2), q1), c00p);
+      else
+        E = ffma2(p0p, ffma2(p0p, q2, q1), c00p);
+      const float2 f = get2(ic<ip>{});
+      const float2 d = ffma2(f2(nw, nw), E, f);  // f - w E
+      put2(ic<ip>{}, ffma2(nom, d, f));        // f - omega (f - w E)
+    });
+  });
+}
+
+// ---------------------------------------------------------------------------------------------
 // the fused step kernel
 // ---------------------------------------------------------------------------------------------
-template <class L, class S, bool GENERAL>
-__global__ void __launch_bounds__(kStepThreads) k_step(const typename S::T* __restrict__ src,
+// Step-kernel variants for float arithmetic.  A cell's populations stay in registers (one pull):
+//   bit 0: scalar arithmetic (0) or mirror pairs in float2 with paired FMA (1);
+//   bit 1: registers as needed, 2 resident blocks of 128 threads per SM (0), or at most 168
+//          registers for 3 resident blocks (1), trading spills for more warps.
+// Double arithmetic pulls each population twice (moments, then collision) and has one variant.
+enum StepVariant : int { kRegScalar = 0, kRegPacked = 1, kRegScalar3 = 2, kRegPacked3 = 3, kNumVariants = 4 };
+
+template <class L, class S, bool GENERAL, int VARIANT>
+__global__ void __launch_bounds__(kStepThreads, (VARIANT & 2) ? 3 : 1) k_step(const typename S::T* __restrict__ src,
                                                        typename S::T* __restrict__ dst,
                                                        const __grid_constant__ StepParams p,
                                                        int* __restrict__ status) {
   using A = typename S::A;
   using ST = typename S::T;
+  constexpr bool PACKED = (VARIANT & 1) && std::is_same<A, float>::value;
+  constexpr bool KEEP = std::is_same<A, float>::value;
   const int gid = blockIdx.x * kStepThreads + threadIdx.x;
   const bool valid = gid < p.cells;
   const Cell cl = make_cell(valid ? gid : p.cells - 1, p);
@@ -404,43 +543,65 @@ __global__ void __launch_bounds__(kStepThreads) k_step(const typename S::T* __re
   // offsets; otherwise resolve periodic wrap / copy-out per population.
   const bool fast = __all_sync(0xffffffffu, is_interior<L>(cl, p));
   const ST* __restrict__ base = src + cl.c;
+  ST* __restrict__ out = dst + cl.c;
 
   auto load = [&](auto I) -> A {
     constexpr int i = decltype(I)::value;
     if (fast) return S::template load<L, i>(base + p.off[i], p);
     return S::template load<L, i>(src + pull_index<L, i, GENERAL>(cl, p), p);
   };
-
-  A fk[S::kKeep ? L::Q : 1];
-  if constexpr (S::kKeep) {
-    static_for<L::Q>([&](auto I) { fk[decltype(I)::value] = load(I); });
-  }
-  auto get = [&](auto I) -> A {
-    if constexpr (S::kKeep) return fk[decltype(I)::value];
-    else return load(I);
+  auto store = [&](auto I, A v) {
+    constexpr int i = decltype(I)::value;
+    if (valid) S::template store<L, i>(out + (long long)i * p.cells, v, p);
   };
 
-  const Mom<A> m = moments<L, A>(get);
+  A fk[KEEP ? L::Q : 1];
+  if constexpr (KEEP) {
+    if (fast) {
+      static_for<L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        fk[i] = S::template load<L, i>(base + p.off[i], p);
+      });
+    } else {
+      static_for<L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        fk[i] = S::template load<L, i>(src + pull_index<L, i, GENERAL>(cl, p), p);
+      });
+    }
+  }
+  auto get = [&](auto I) -> A {
+    if constexpr (KEEP) return fk[decltype(I)::value];
+    else return load(I);
+  };
+  auto get2 = [&](auto I) -> float2 {
+    constexpr int i = decltype(I)::value;
+    return make_float2((float)get(ic<i>{}), (float)get(ic<i + 1>{}));
+  };
+
+  Mom<A> m;
+  if constexpr (PACKED) m = moments_f2<L>(get2);
+  else m = moments<L, A>(get);
   const Landau<A> lw = landau_step<A>(m, p);
-  ST* __restrict__ out = dst + cl.c;
   if (!lw.ok) {
     // no Landau frame: record it and stream the populations without collision
     if (valid) {
       atomicAdd(&status[kStatusNonconv], 1);
-      static_for<L::Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        S::template store<L, i>(out + (long long)i * p.cells, get(I), p);
-      });
+      static_for<L::Q>([&](auto I) { store(I, get(I)); });
     }
     return;
   }
   const A T = lw.eps / (A(3) * lw.n);
   const A inv_tau = A(1) / tau_prime<A>(T, p);
-  auto put = [&](auto I, A v) {
-    constexpr int i = decltype(I)::value;
-    if (valid) S::template store<L, i>(out + (long long)i * p.cells, v, p);
-  };
-  collide<L, A>(lw, T, inv_tau, get, put);
+  if constexpr (PACKED) {
+    auto put2 = [&](auto I, float2 v) {
+      constexpr int i = decltype(I)::value;
+      store(ic<i>{}, v.x);
+      store(ic<i + 1>{}, v.y);
+    };
+    collide_f2<L>(lw, T, inv_tau, get2, put2);
+  } else {
+    collide<L, A>(lw, T, inv_tau, get, store);
+  }
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -7,12 +7,14 @@ namespace rlb {
 struct StepParams;
 
 struct Launchers {
-  cudaError_t (*step)(const void* src, void* dst, const StepParams& p, int* status, bool general, cudaStream_t s);
+  cudaError_t (*step)(const void* src, void* dst, const StepParams& p, int* status, bool general, int variant,
+                      cudaStream_t s);
   cudaError_t (*fields)(const void* src, const StepParams& p, double* fields, double* partial, int* status, bool pull,
                         cudaStream_t s);
   cudaError_t (*init)(const double* n, const double* T, const double* u, void* dst, const StepParams& p, int* status,
                       cudaStream_t s);
   cudaError_t (*convert)(void* pop, double* dbl, int i0, int i1, bool to_f64, const StepParams& p, cudaStream_t s);
+  int step_variants;  // number of step-kernel variants the autotuner may choose from
 };
 
 #define RLB_DECLARE_LAUNCHERS(ORDER, STORAGE) extern const Launchers launchers_o##ORDER##_s##STORAGE;

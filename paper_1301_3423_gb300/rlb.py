@@ -41,6 +41,7 @@ class Params(ctypes.Structure):
         ("landau_fp64", ctypes.c_int),
         ("gamma_thr", ctypes.c_double),
         ("n_ref", ctypes.c_double),
+        ("step_variant", ctypes.c_int),
         ("stream", ctypes.c_void_p),
         ("q", ctypes.c_int),
         ("vel", ctypes.POINTER(ctypes.c_int)),
@@ -53,7 +54,7 @@ class Params(ctypes.Structure):
 _LIB = None
 DECLARED = ["rlb_default_params", "rlb_bytes_required", "rlb_create", "rlb_init", "rlb_step", "rlb_moments",
             "rlb_sync", "rlb_get_populations", "rlb_set_populations", "rlb_steps_done", "rlb_kernel_launches",
-            "rlb_destroy", "rlb_last_error", "rlb_quadrature"]
+            "rlb_destroy", "rlb_last_error", "rlb_quadrature", "rlb_autotune"]
 
 
 def lib_path():
@@ -98,6 +99,8 @@ def load(build_if_missing=True):
                                    ctypes.POINTER(ctypes.POINTER(ctypes.c_int)), ctypes.POINTER(dp),
                                    ctypes.POINTER(dp)]
     lib.rlb_quadrature.restype = ip
+    lib.rlb_autotune.argtypes = [vp, ip, ctypes.POINTER(ip), dp]
+    lib.rlb_autotune.restype = ip
     _LIB = lib
     return lib
 
@@ -160,7 +163,7 @@ class RLB:
 
     def __init__(self, shape, order=3, bc=("periodic", "periodic", "periodic"), eta_over_s=0.1, tau_prime=0.0,
                  tau_local_T=True, T_ref=1.0, dx_fm=0.008, T_unit_GeV=0.4, storage="f64", landau_fp64=False,
-                 gamma_thr=2.0, n_ref=1.0, stream=None, quadrature=None):
+                 gamma_thr=2.0, n_ref=1.0, stream=None, quadrature=None, step_variant=-1):
         self._lib = load()
         nz, ny, nx = shape
         p = Params()
@@ -172,6 +175,7 @@ class RLB:
         p.T_ref, p.dx_fm, p.T_unit_GeV = T_ref, dx_fm, T_unit_GeV
         p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
         p.landau_fp64, p.gamma_thr, p.n_ref = int(bool(landau_fp64)), gamma_thr, n_ref
+        p.step_variant = int(step_variant)
         if stream is not None:
             p.stream = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
         self._keep = []
@@ -267,6 +271,13 @@ class RLB:
         self._check(self._lib.rlb_set_populations(self._h, p, dev))
         if dev:
             self.sync()
+
+    def autotune(self, reps=5):
+        """rlb_autotune: (chosen variant, ms per step of each variant)."""
+        v = ctypes.c_int()
+        ms = (ctypes.c_double * 4)()
+        self._check(self._lib.rlb_autotune(self._h, int(reps), ctypes.byref(v), ms))
+        return v.value, list(ms)
 
     @property
     def steps_done(self):

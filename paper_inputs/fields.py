@@ -37,10 +37,11 @@ def _band_field(shape, kmax, rng):
     return np.real(np.fft.ifftn(spec)) * spec.size
 
 
-def smooth_random_fields(shape, seed=1, vmax=0.6, sigma_lnT=0.2, kmax=4):
+def smooth_random_fields(shape, seed=1, vmax=0.6, sigma_lnT=0.2, kmax=4, density="cube"):
     """Random-field throughput case: velocity from Fourier modes |k| <= kmax (seed), rescaled to
     max |v| = vmax; T = exp(sigma g - sigma^2/2) with g a unit-variance field of the same band
-    (seed + 1), so mean T ~ 1; n = T^3."""
+    (seed + 1), so mean T ~ 1; density "cube": n = T^3 (pressure n T = T^4), "uniform": n = 1
+    (pressure T)."""
     rng = np.random.default_rng(seed)
     u = np.stack([_band_field(shape, kmax, rng) for _ in range(3)])
     vnorm = np.sqrt((u * u).sum(axis=0)).max()
@@ -49,4 +50,6 @@ def smooth_random_fields(shape, seed=1, vmax=0.6, sigma_lnT=0.2, kmax=4):
     sd = g.std()
     g = g / sd if sd > 0 else g
     T = np.exp(sigma_lnT * g - 0.5 * sigma_lnT ** 2)
+    if density == "uniform":
+        return np.ones(shape), T, u
     return T ** 3, T, u

@@ -38,7 +38,7 @@ def test_params_layout_matches_c():
     assert (p.order, p.nx, p.ny, p.nz, list(p.bc)) == (3, 1, 1, 1, [0, 0, 0])
     assert (p.eta_over_s, p.tau_prime, p.tau_local_T, p.T_ref) == (0.1, 0.0, 1, 1.0)
     assert (p.dx_fm, p.T_unit_GeV, p.storage, p.landau_fp64) == (0.008, 0.4, 0, 0)
-    assert (p.gamma_thr, p.n_ref, p.stream, p.q) == (2.0, 1.0, None, 0)
+    assert (p.gamma_thr, p.n_ref, p.step_variant, p.stream, p.q) == (2.0, 1.0, -1, None, 0)
 
 
 @pytest.mark.parametrize("order", [3, 2])
@@ -61,7 +61,7 @@ def test_bytes_required():
 
 
 @pytest.mark.parametrize("bad", [dict(order=4), dict(nx=0), dict(storage=7), dict(eta_over_s=-1.0),
-                                 dict(gamma_thr=0.5), dict(bc=(0, 2, 0))])
+                                 dict(gamma_thr=0.5), dict(bc=(0, 2, 0)), dict(step_variant=4)])
 def test_create_rejects_invalid_parameters(bad):
     """Validation happens on the host before any device call."""
     kw = dict(shape=(4, 4, 4))

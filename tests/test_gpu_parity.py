@@ -145,22 +145,24 @@ def test_riemann_tube_full_run(order):
     assert max(en, ee, eu) < 1e-12
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("order", [3, 2])
-def test_f32_fields_within_1e5(order):
+def test_f32_fields_within_1e5(order, variant):
     """Float storage and arithmetic: Landau fields within 1e-5 of the FP64 oracle after 40 steps of
-    the random-field case (|v| <= 0.6, sigma_lnT = 0.2, eta/s = 0.1)."""
+    the random-field case (|v| <= 0.6, sigma_lnT = 0.2, eta/s = 0.1), for every step-kernel variant
+    (registers or two pulls, scalar or paired arithmetic)."""
     lat = oracle.read_lattice(order)
     shape = (11, 13, 17)
     n, T, u = gen.smooth_random_fields(shape, seed=31, vmax=0.6, sigma_lnT=0.2)
     o = oracle.OracleRLB(lat, shape[2], shape[1], shape[0], eta_over_s=0.1)
     o.init(n, T, u)
     o.step(40)
-    with RLB(shape, order=order, storage="f32", eta_over_s=0.1) as g:
+    with RLB(shape, order=order, storage="f32", eta_over_s=0.1, step_variant=variant) as g:
         g.init(n, T, u)
         g.step(40)
         m = g.moments()
     en, ee, eu = field_err(o.moments(), m)
-    print("f32 order %d: n %.2e eps %.2e u %.2e" % (order, en, ee, eu))
+    print("f32 order %d variant %d: n %.2e eps %.2e u %.2e" % (order, variant, en, ee, eu))
     assert max(en, ee, eu) < 1e-5
 
 
@@ -191,6 +193,21 @@ def test_conservation_on_gpu(storage, tol):
         g.step(60)
         t1 = g.moments()["totals"]
     assert np.max(np.abs(t1 - t0)) <= tol * np.abs(t0).max()
+
+
+def test_autotune_keeps_the_state_and_picks_a_variant():
+    shape = (20, 24, 64)
+    n, T, u = gen.smooth_random_fields(shape, seed=3, vmax=0.4)
+    with RLB(shape, storage="f32") as a, RLB(shape, storage="f32") as b:
+        a.init(n, T, u)
+        b.init(n, T, u)
+        v, ms = a.autotune(reps=2)
+        assert 0 <= v <= 3 and all(t > 0 for t in ms)
+        assert np.array_equal(a.populations(), b.populations())  # autotuning changed nothing
+        a.step(1)
+        with pytest.raises(RLBError) as e:
+            a.autotune()
+        assert e.value.status == rlbmod.RLB_ESTATE
 
 
 def test_checkpoint_resume_is_bitwise():
@@ -248,8 +265,9 @@ def test_landau_failure_is_reported_not_hidden():
         assert np.array_equal(g.populations()[0], single[0])  # streamed, not collided
 
 
-@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 2e-5)])
-def test_full_size_sampled_cells(storage, tol):
+@pytest.mark.parametrize("storage,tol,variant", [("f64", 1e-12, -1), ("f32", 2e-5, 0), ("f32", 2e-5, 1),
+                                                 ("f32", 2e-5, 2), ("f32", 2e-5, 3)])
+def test_full_size_sampled_cells(storage, tol, variant):
     """256^3 random-field case in the benchmark's launch configuration: one step from the seeded
     equilibrium, 96 cells (corners, faces, interior, random) against the oracle cell by cell."""
     lat = oracle.read_lattice(3)
@@ -262,7 +280,7 @@ def test_full_size_sampled_cells(storage, tol):
     sample = np.array(flat, dtype=np.int64)
     o = oracle.OracleRLB(lat, N, N, N, eta_over_s=0.1)
     ref = o.init_step_cells(n, T, u, sample)
-    with RLB(shape, order=3, storage=storage, eta_over_s=0.1) as g:
+    with RLB(shape, order=3, storage=storage, eta_over_s=0.1, step_variant=variant) as g:
         g.init(n, T, u)
         g.step(1)
         dev = torch.empty((lat.q, N ** 3), dtype=torch.float64, device="cuda")
@@ -271,5 +289,5 @@ def test_full_size_sampled_cells(storage, tol):
         del dev
     scale = np.maximum(np.abs(ref), lat.w[None, :] * n.max() / 2)
     err = float(np.max(np.abs(got - ref) / scale))
-    print("full-size %s sampled error %.2e" % (storage, err))
+    print("full-size %s variant %d sampled error %.2e" % (storage, variant, err))
     assert err < tol
