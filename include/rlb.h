@@ -156,8 +156,35 @@ long rlb_kernel_launches(const rlb_ctx* ctx);
 rlb_status rlb_destroy(rlb_ctx* ctx);
 
 /* Text of the context's most recent error ("" if none).  Valid until the next call on ctx.
- * With ctx == NULL: the most recent rlb_create failure of the calling thread. */
+ * With ctx == NULL: the most recent failure of a call without a context (rlb_create,
+ * rlb_totals_noalloc) on the calling thread. */
 const char* rlb_last_error(const rlb_ctx* ctx);
+
+/* Largest lattice rlb_totals_noalloc accepts: 65536 blocks of 128 cells. */
+#define RLB_NOALLOC_MAX_CELLS 8388608
+
+/* Conserved totals of a caller-owned population buffer, computed without allocating anything.
+ * The paper has no counterpart; this exists for callers that cannot allocate device memory, such
+ * as code recording into a stream capture that must not gain allocation nodes, plug-ins whose host
+ * owns every allocation, or processes whose memory pools already hold the whole device.
+ *
+ * f is a device buffer of q * nx * ny * nz populations in the layout and precision of `storage`
+ * (the layout of the context buffers: [q][cells], x fastest; RLB_F16DEV stores f_i / w_i - n_ref/2).
+ * totals[5] (host) receives sum over cells of N^0, T^00, T^0x, T^0y, T^0z of these populations,
+ * the same sums rlb_moments reports before the first step.  The call enqueues two kernels on
+ * `stream` (NULL: default stream), copies the 5 sums to totals and synchronises the stream.
+ *
+ * Scratch: a fixed device array inside the library (RLB_NOALLOC_MAX_CELLS / 128 * 5 + 5 doubles,
+ * about 2.6 MB) that every device loading the library holds until the process exits.  No
+ * cudaMalloc, cudaFree or other allocating routine is called.  The first call on a device looks up
+ * that array's device address, with the device current; make that first call before any stream
+ * capture.  Every call shares the array: calls whose work overlaps on the GPU (other streams, other
+ * host threads) race and must be serialised by the caller.  Nothing in it needs to start at zero.
+ *
+ * Errors: RLB_EINVAL (order, storage, null pointer, empty lattice, or more than
+ * RLB_NOALLOC_MAX_CELLS cells; rlb_last_error(NULL) explains), RLB_ECUDA. */
+rlb_status rlb_totals_noalloc(int order, int storage, int nx, int ny, int nz, double n_ref, const void* f,
+                              double totals[5], void* stream);
 
 /* The quadrature built into the library for order 2 or 3 (Sec. II.C, App. A): q populations with
  * velocities vel[q][3], energy levels, energies p0 and weights w.  The arrays are static and owned

@@ -69,6 +69,8 @@ def build(force=False, verbose=False):
     nvcc = _nvcc()
     inc = ["-I", INCLUDE, "-I", BUILD, "-I", CSRC]
     jobs = [(os.path.join(BUILD, "rlb_api.o"), [nvcc] + NVCC_FLAGS + inc + ["-c", os.path.join(CSRC, "rlb_api.cu")])]
+    jobs.append((os.path.join(BUILD, "rlb_noalloc.o"), [nvcc] + NVCC_FLAGS + inc + [
+        "-c", os.path.join(CSRC, "rlb_noalloc.cu"), "-o", os.path.join(BUILD, "rlb_noalloc.o")]))
     for o, s in INSTANCES:
         obj = os.path.join(BUILD, "rlb_inst_o%d_s%d.o" % (o, s))
         jobs.append((obj, [nvcc] + NVCC_FLAGS + inc + ["-DRLB_INST_ORDER=%d" % o, "-DRLB_INST_STORAGE=%d" % s,

@@ -65,6 +65,11 @@ struct rlb_ctx {
 // Errors of calls that have no context (rlb_create with invalid parameters) are kept per thread.
 static thread_local std::string g_create_err;
 
+namespace rlb {
+// Sets the text rlb_last_error(NULL) returns on this thread (used by context-free entry points).
+__attribute__((visibility("hidden"))) void set_thread_error(const std::string& msg) { g_create_err = msg; }
+}  // namespace rlb
+
 static rlb_status fail(rlb_ctx* c, rlb_status st, const std::string& msg) {
   if (c) c->err = msg;
   else g_create_err = msg;

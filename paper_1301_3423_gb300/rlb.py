@@ -54,7 +54,7 @@ class Params(ctypes.Structure):
 _LIB = None
 DECLARED = ["rlb_default_params", "rlb_bytes_required", "rlb_create", "rlb_init", "rlb_step", "rlb_moments",
             "rlb_sync", "rlb_get_populations", "rlb_set_populations", "rlb_steps_done", "rlb_kernel_launches",
-            "rlb_destroy", "rlb_last_error", "rlb_quadrature", "rlb_autotune"]
+            "rlb_destroy", "rlb_last_error", "rlb_quadrature", "rlb_autotune", "rlb_totals_noalloc"]
 
 
 def lib_path():
@@ -101,6 +101,8 @@ def load(build_if_missing=True):
     lib.rlb_quadrature.restype = ip
     lib.rlb_autotune.argtypes = [vp, ip, ctypes.POINTER(ip), dp]
     lib.rlb_autotune.restype = ip
+    lib.rlb_totals_noalloc.argtypes = [ip, ip, ip, ip, ip, ctypes.c_double, vp, dp, vp]
+    lib.rlb_totals_noalloc.restype = ip
     _LIB = lib
     return lib
 
@@ -118,6 +120,22 @@ def quadrature(order):
     n = q.value
     return dict(v=np.ctypeslib.as_array(v, (n, 3)).copy(), level=np.ctypeslib.as_array(lev, (n,)).copy(),
                 p0=np.ctypeslib.as_array(p0, (n,)).copy(), w=np.ctypeslib.as_array(w, (n,)).copy())
+
+
+def totals_noalloc(f, order, storage, shape, n_ref=1.0, stream=None):
+    """rlb_totals_noalloc: sum over cells of N^0, T^00, T^0x, T^0y, T^0z of the populations in the
+    CUDA tensor ``f`` (storage layout [q][cells]), with no allocation inside the library."""
+    lib = load()
+    nz, ny, nx = shape
+    st_code = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    if not _is_cuda_tensor(f) or not f.is_contiguous():
+        raise ValueError("f must be a contiguous CUDA tensor")
+    tot = (ctypes.c_double * 5)()
+    sp = None if stream is None else ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    st = lib.rlb_totals_noalloc(order, st_code, nx, ny, nz, n_ref, ctypes.c_void_p(f.data_ptr()), tot, sp)
+    if st != RLB_OK:
+        raise RLBError(st, lib.rlb_last_error(None).decode())
+    return np.array(tot[:])
 
 
 def read_quadrature_file(path):
