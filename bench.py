@@ -143,6 +143,118 @@ def cpu_baseline(n, T, u, budget_s=12.0, planes=2):
                       "(%d cells; serial FP64 C oracle, %.1f s)" % (steps, planes, nx, ny, nx, nx, ny, nz, cells, dt)}
 
 
+def field_errors(ref, got):
+    """n, eps pointwise relative; u as max|du| / max(max|u_ref|, 0.01)."""
+    en = float(np.max(np.abs(got["n"] - ref["n"]) / np.abs(ref["n"])))
+    ee = float(np.max(np.abs(got["eps"] - ref["eps"]) / np.abs(ref["eps"])))
+    ur = ref["U"][1:] / ref["U"][0]
+    ug = got["U"][1:] / got["U"][0]
+    du = float(np.max(np.sqrt(((ug - ur) ** 2).sum(axis=0))))
+    return {"n_rel": en, "eps_rel": ee, "u_rel": du / max(float(np.max(np.sqrt((ur ** 2).sum(axis=0)))), 0.01)}
+
+
+def batched_instances(scale, seed=4, count=64):
+    """The batched workload: `count` instances drawn by seed from shock tubes 1x1xN (N in 400..4000,
+    copy-out ends, 500 steps) and 32^3..128^3 periodic shear (2000 steps) or random-field (1000
+    steps) boxes, eta/s in {0.01, 0.1, 0.5}; step counts times `scale`."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        kind = str(rng.choice(["tube", "shear", "random"]))
+        eta = float(rng.choice([0.01, 0.1, 0.5]))
+        if kind == "tube":
+            N = int(rng.integers(400, 4001))
+            shape, bc, steps = (N, 1, 1), (0, 0, 1), 500
+        else:
+            L = int(rng.choice([32, 48, 64, 96, 128]))
+            shape, bc, steps = (L, L, L), (0, 0, 0), (2000 if kind == "shear" else 1000)
+        out.append((kind, shape, bc, eta, max(1, int(round(steps * scale))), int(rng.integers(1 << 30))))
+    return out
+
+
+def make_instance(spec, storage, variant=-1, stream=None):
+    from paper_1301_3423_gb300 import RLB
+    kind, shape, bc, eta, steps, seed = spec
+    c = RLB(shape, order=ORDER, bc=bc, eta_over_s=eta, storage=storage, landau_fp64=(storage != "f64"),
+            step_variant=variant, stream=stream)
+    if kind == "tube":
+        f = gen.riemann_tube(shape[0])
+    elif kind == "shear":
+        f = gen.shear_wave(shape[2], amp=0.05, ny=shape[1], nz=shape[0])
+    else:
+        f = gen.smooth_random_fields(shape, seed=seed, vmax=0.4, sigma_lnT=0.15, kmax=2, density="uniform")
+    c.init(*f)
+    return c
+
+
+def run_batched(args, stream):
+    """64 uneven instances stepped together (persistent tile-queue kernel, CUDA-graph step loops),
+    against the same instances stepped one at a time in float and in double."""
+    import torch
+
+    from paper_1301_3423_gb300 import Batch
+    specs = batched_instances(args.batch_scale)
+    updates = float(sum(np.prod(sp[1]) * sp[4] for sp in specs))
+    ctxs = [make_instance(sp, "f32", stream=stream) for sp in specs]
+    b = Batch(ORDER, "f32", stream=stream)
+    for c, sp in zip(ctxs, specs):
+        b.add(c, sp[4])
+    variant, _ = b.autotune(reps=2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    active = len(ctxs)
+    while active:
+        active = b.run(25, graph=True)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    for c in ctxs:
+        c.sync()
+        c.close()
+    launches = b.kernel_launches
+    b.close()
+    t_seq = 0.0  # only the stepping counts, as for the batch
+    for sp in specs:
+        c = make_instance(sp, "f32", variant=variant, stream=stream)
+        c.sync()
+        t1 = time.perf_counter()
+        c.step(sp[4])
+        c.sync()
+        t_seq += time.perf_counter() - t1
+        c.close()
+    sub = specs[:8]  # double storage is FP64-ALU bound: timed on the first 8 instances
+    u64 = float(sum(np.prod(sp[1]) * sp[4] for sp in sub))
+    t64 = 0.0
+    for sp in sub:
+        c = make_instance(sp, "f64", stream=stream)
+        c.sync()
+        t1 = time.perf_counter()
+        c.step(sp[4])
+        c.sync()
+        t64 += time.perf_counter() - t1
+        c.close()
+    return {"instances": len(specs), "cell_updates": updates, "step_scale": args.batch_scale,
+            "value": updates / t_batch / 1e6, "unit": "MLUPS", "seconds": t_batch, "solves_per_s": len(specs) / t_batch,
+            "variant": variant, "kernel_launches": launches, "graph_steps": 25,
+            "sequential_f32": {"value": updates / t_seq / 1e6, "seconds": t_seq, "solves_per_s": len(specs) / t_seq},
+            "fp64_plain": {"value": u64 / t64 / 1e6, "instances": len(sub), "seconds": t64,
+                           "solves_per_s_est": len(specs) / (t64 * updates / u64)}}
+
+
+def run_serving(args, stream):
+    """Poisson request stream (mean 20 / s) through the continuous-batching server."""
+    from paper_1301_3423_gb300 import serve
+    reqs = serve.poisson_requests(60, rate=20.0, seed=5, step_scale=args.batch_scale, f16_fraction=0.3)
+    srv = serve.Server(hbm_budget=150e9, chunk=25, stream=stream)
+    try:
+        st = srv.run(reqs, realtime=True, max_wall=600)
+    finally:
+        srv.close()
+    st.update({"rate_per_s": 20.0, "step_scale": args.batch_scale,
+               "largest_side": max(max(r.shape) if r.kind != "tube" else 0 for r in reqs),
+               "f16dev_requests": sum(r.storage == "f16dev" for r in reqs)})
+    return st
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -169,6 +281,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--variant", type=int, default=-1, help="force a step-kernel variant instead of autotuning")
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--batch-scale", type=float, default=0.1,
+                    help="fraction of the batched / served step counts (500 / 2000 / 1000) to run")
     ap.add_argument("--density", default=DENSITY, choices=["uniform", "cube"],
                     help="initial density: uniform n = 1, or n = T^3")
     ap.add_argument("--sigma", type=float, default=SIGMA_LNT, help="std of ln T")
@@ -181,6 +299,7 @@ def main():
     import torch
 
     from paper_1301_3423_gb300 import RLB
+    from paper_1301_3423_gb300.rlb import VARIANT_NAMES
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
     N = args.n
@@ -202,9 +321,12 @@ def main():
         return float(t.item())
 
     # ---- device-resident throughput (the headline value) ------------------------------------
-    g = RLB(shape, order=ORDER, storage="f32", eta_over_s=ETA_S, stream=stream)
+    g = RLB(shape, order=ORDER, storage="f32", eta_over_s=ETA_S, stream=stream, step_variant=args.variant)
     g.init(n, T, u)
-    variant, variant_ms = g.autotune(reps=3)
+    if args.variant < 0:
+        variant, variant_ms = g.autotune(reps=3)
+    else:
+        variant, variant_ms = args.variant, []
     g.step(args.warmup)
     g.sync()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -225,10 +347,12 @@ def main():
     ms_total_max = max_over_ranks(ms_total)
     g.sync()  # raises if any cell lost its Landau frame: a broken simulation is not a measurement
     value = world * cells * args.steps / (ms_total_max * 1e-3) / 1e6
-    per_launch_s = ms_total * 1e-3 / launches
+    # A step is one launch of the interior kernel plus one of the shell kernel (disjoint cells):
+    # the roofline takes the algorithmic bytes of the whole step over the step's device time.
+    per_step_s = ms_total * 1e-3 / args.steps
     algo_bytes = cells * Q * 2 * 4
     peaks, peak_src = measured_peaks()
-    achieved = algo_bytes / per_launch_s / 1e9
+    achieved = algo_bytes / per_step_s / 1e9
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "step_f32_traffic.json")
     if os.path.exists(tpath):
@@ -255,6 +379,21 @@ def main():
         g64.close()
         fp64 = {"value": world * cells * k64 / (ms64 * 1e-3) / 1e6, "unit": "MLUPS", "steps": k64,
                 "ms_per_step": ms64 / k64, "bound": "fp64 alu"}
+
+    # ---- float against double fields after the same steps -------------------------------------
+    accuracy = None
+    if not args.no_accuracy:
+        ka = 30
+        res = {}
+        for st_name in ("f32", "f64"):
+            ga = RLB(shape, order=ORDER, storage=st_name, eta_over_s=ETA_S, stream=stream,
+                     step_variant=(variant if st_name == "f32" else -1))
+            ga.init(n, T, u)
+            ga.step(ka)
+            res[st_name] = ga.moments()
+            ga.close()
+        accuracy = dict(steps=ka, **field_errors(res["f64"], res["f32"]))
+        del res
 
     # ---- end to end through the C ABI from pinned host buffers -------------------------------
     e2e = None
@@ -283,6 +422,8 @@ def main():
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                "job": "rlb_init from pinned host fields + %d steps + rlb_moments to host" % args.steps}
 
+    batched = None if args.no_batch else run_batched(args, stream)
+    serving = None if args.no_serve else run_serving(args, stream)
     if rank != 0:
         return
     cb = None if args.no_cpu_baseline else cpu_baseline(n, T, u)
@@ -296,15 +437,18 @@ def main():
                    "baseline_metric": BASELINE_METRIC},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                     "peak_source": peak_src, "algorithmic_bytes_per_launch": algo_bytes,
-                     "kernel": "k_step<Quad3, StoreF32, variant %d>" % variant, "launch_ms": per_launch_s * 1e3},
+                     "peak_source": peak_src, "algorithmic_bytes_per_step": algo_bytes,
+                     "kernel": "k_step_interior + k_step_shell <Quad3, StoreF32, variant %d>" % variant,
+                     "step_ms": per_step_s * 1e3, "launches_per_step": launches / args.steps},
         "cpu_baseline": cb,
         "e2e": e2e,
         "fp64_plain": fp64,
+        "accuracy_f32_vs_f64": accuracy,
+        "batched": batched,
+        "serving": serving,
         "gpu_launches": launches,
         "autotune": {"variant": variant, "ms_per_step": variant_ms,
-                     "variants": ["scalar, 2 blocks/SM", "paired, 2 blocks/SM", "scalar, 3 blocks/SM",
-                                  "paired, 3 blocks/SM"]},
+                     "variants": VARIANT_NAMES[:len(variant_ms)]},
         "clocks": clk.summary(),
         "wall_s_timed_region": t_wall,
     }

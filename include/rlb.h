@@ -79,7 +79,7 @@ typedef struct {
                          are solved in double (default 2.0) */
   double n_ref;       /* RLB_F16DEV only: reference density of the stored deviation (default 1.0) */
   int step_variant;   /* float storage only: -1 = library default, or force a step-kernel variant
-                         0..3 (see rlb_autotune); ignored for RLB_F64 */
+                         (see rlb_autotune); ignored for RLB_F64 */
   void* stream;       /* cudaStream_t to enqueue on; NULL = the default stream */
   /* Optional quadrature (Sec. II.C, App. A).  When q > 0 these arrays are compared with the
    * quadrature compiled into the library for this order and must match exactly (RLB_EINVAL
@@ -136,15 +136,70 @@ rlb_status rlb_get_populations(rlb_ctx* ctx, double* f, int on_device);
  * their own fields.  Errors: RLB_EINVAL, RLB_ECUDA. */
 rlb_status rlb_set_populations(rlb_ctx* ctx, const double* f, int on_device);
 
-/* Autotuner: time every step-kernel variant of this context (for float storage: scalar or paired
- * float arithmetic, 2 or 3 resident blocks per SM) on the context's own lattice
- * and keep the fastest for later rlb_step calls.  Each variant repeats one step from the current
- * populations into the spare buffer `reps` times, so the state does not change; this is allowed
- * only before the first step after rlb_init / rlb_set_populations (RLB_ESTATE otherwise).
- * *variant (may be NULL) receives the choice; ms[4] (may be NULL) the measured milliseconds per
- * step of each variant (0 where a variant does not exist).  Synchronises the stream.
+/* Upper bound on the number of step-kernel variants. */
+#define RLB_MAX_VARIANTS 8
+
+/* Autotuner: time every step-kernel variant of this context on the context's own lattice and keep
+ * the fastest for later rlb_step calls.  For float storage the variants differ in arithmetic
+ * (scalar, or mirror pairs in paired-FMA float2) and residency (all populations in registers at 2
+ * or 3 resident blocks per SM, or part of them staged in shared memory at 4); double storage has
+ * one.  Each variant repeats one step from the current populations into the spare buffer `reps`
+ * times, so the state does not change; this is allowed only before the first step after rlb_init
+ * / rlb_set_populations (RLB_ESTATE otherwise).  *variant (may be NULL) receives the choice;
+ * ms[RLB_MAX_VARIANTS] (may be NULL) the milliseconds per step of each variant (0 where a
+ * variant does not exist).  Synchronises the stream.
  * Errors: RLB_EINVAL (reps < 1), RLB_ESTATE, RLB_ECUDA. */
-rlb_status rlb_autotune(rlb_ctx* ctx, int reps, int* variant, double ms[4]);
+rlb_status rlb_autotune(rlb_ctx* ctx, int reps, int* variant, double ms[RLB_MAX_VARIANTS]);
+
+/* ---------------------------------------------------------------------------------------------
+ * Batched stepping.  A batch steps many contexts of the same order and storage together: each
+ * launch of a persistent kernel advances every member with steps left by one time step of
+ * Eq. (rlb:disc), taking tiles of 128 cells from one queue shared by all members, so lattices of
+ * very different sizes fill the GPU together.  Members keep their own buffers, parameters, status
+ * and step counters; a member's populations after a batched run are bitwise those of the same
+ * steps taken alone with the same step-kernel variant.  Members must use the batch's stream.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct rlb_batch rlb_batch;
+
+/* Create an empty batch for order 2/3 and storage RLB_F64/F32/F16DEV on the current device,
+ * enqueuing on `stream` (NULL: default stream).  Errors: RLB_EINVAL, RLB_ENOMEM, RLB_ECUDA. */
+rlb_status rlb_batch_create(int order, int storage, void* stream, rlb_batch** out);
+
+/* Add ctx as a member that is to take `steps` more steps; *slot (may be NULL) receives its slot.
+ * The batch does not own the context; keep it alive while it is a member.  Errors: RLB_EINVAL
+ * (order / storage mismatch, already a member, steps < 0). */
+rlb_status rlb_batch_add(rlb_batch* b, rlb_ctx* ctx, long steps, int* slot);
+
+/* Remove the member in `slot`; its context keeps its state.  Errors: RLB_EINVAL. */
+rlb_status rlb_batch_remove(rlb_batch* b, int slot);
+
+/* Steps the member in `slot` still has to take (-1 for an empty slot). */
+long rlb_batch_steps_left(const rlb_batch* b, int slot);
+
+/* Enqueue up to nsteps steps: launch k advances every member with more than k steps left, so each
+ * member stops at its own count.  use_graph = 1 captures the nsteps launches once as a CUDA graph
+ * and replays it while the member set and nsteps are unchanged.  *active (may be NULL) receives the
+ * number of members with steps left afterwards.  Asynchronous; member failures are reported by the
+ * members' own synchronising calls.  Errors: RLB_EINVAL, RLB_ENOMEM, RLB_ECUDA. */
+rlb_status rlb_batch_run(rlb_batch* b, long nsteps, int use_graph, int* active);
+
+/* Autotuner for the batch: time every step-kernel variant of the batched kernel on the current
+ * members (each repetition recomputes the members' next state into their spare buffers, so no
+ * state changes; allowed only while no member has taken a step, RLB_ESTATE otherwise) and keep the
+ * fastest.  *variant and ms[RLB_MAX_VARIANTS] as for rlb_autotune. */
+rlb_status rlb_batch_autotune(rlb_batch* b, int reps, int* variant, double ms[RLB_MAX_VARIANTS]);
+
+/* Force the batched kernel's step variant (the one rlb_autotune / step_variant number). */
+rlb_status rlb_batch_set_variant(rlb_batch* b, int variant);
+
+/* Kernel launches the batch has enqueued (-1 for NULL). */
+long rlb_batch_kernel_launches(const rlb_batch* b);
+
+/* Text of the batch's most recent error. */
+const char* rlb_batch_last_error(const rlb_batch* b);
+
+/* Release the batch (not its members' contexts).  Synchronises its stream.  NULL is accepted. */
+rlb_status rlb_batch_destroy(rlb_batch* b);
 
 /* Number of time steps taken since rlb_init / rlb_set_populations (-1 for NULL). */
 long rlb_steps_done(const rlb_ctx* ctx);

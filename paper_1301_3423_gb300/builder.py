@@ -22,6 +22,8 @@ LATTICE = os.path.join(ROOT, "lattice")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
 INSTANCES = [(o, s) for o in (3, 2) for s in (0, 1, 2)]
+# step-kernel variants compiled per (order, storage): one for double storage, four for float ones
+VARIANT_UNITS = [(o, s, v) for o, s in INSTANCES for v in ((0,) if s == 0 else (0, 1, 2, 3))]
 
 
 def _nvcc():
@@ -69,15 +71,24 @@ def build(force=False, verbose=False):
     nvcc = _nvcc()
     inc = ["-I", INCLUDE, "-I", BUILD, "-I", CSRC]
     jobs = [(os.path.join(BUILD, "rlb_api.o"), [nvcc] + NVCC_FLAGS + inc + ["-c", os.path.join(CSRC, "rlb_api.cu")])]
+    jobs.append((os.path.join(BUILD, "rlb_batch.o"), [nvcc] + NVCC_FLAGS + inc + [
+        "-c", os.path.join(CSRC, "rlb_batch.cu"), "-o", os.path.join(BUILD, "rlb_batch.o")]))
     jobs.append((os.path.join(BUILD, "rlb_noalloc.o"), [nvcc] + NVCC_FLAGS + inc + [
         "-c", os.path.join(CSRC, "rlb_noalloc.cu"), "-o", os.path.join(BUILD, "rlb_noalloc.o")]))
     for o, s in INSTANCES:
         obj = os.path.join(BUILD, "rlb_inst_o%d_s%d.o" % (o, s))
         jobs.append((obj, [nvcc] + NVCC_FLAGS + inc + ["-DRLB_INST_ORDER=%d" % o, "-DRLB_INST_STORAGE=%d" % s,
                                                           "-c", os.path.join(CSRC, "rlb_inst.cu"), "-o", obj]))
+    for o, s, v in VARIANT_UNITS:
+        obj = os.path.join(BUILD, "rlb_inst_o%d_s%d_v%d.o" % (o, s, v))
+        jobs.append((obj, [nvcc] + NVCC_FLAGS + inc + ["-DRLB_INST_ORDER=%d" % o, "-DRLB_INST_STORAGE=%d" % s,
+                                                          "-DRLB_INST_VARIANT=%d" % v, "-c",
+                                                          os.path.join(CSRC, "rlb_inst_variant.cu"), "-o", obj]))
+    # longest units first so the parallel build ends sooner
+    jobs = jobs[:1] + sorted(jobs[1:], key=lambda j: ("_v" not in j[0], "_s0" in j[0]))
     jobs[0][1].extend(["-o", jobs[0][0]])
     logs = []
-    with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(len(jobs), max(os.cpu_count() or 4, 4))) as ex:
         for out in ex.map(lambda j: _run(j[1]), jobs):
             logs.append(out)
     tmp = LIB + ".%d.tmp" % os.getpid()

@@ -8,6 +8,7 @@
 
 #include "rlb.h"
 #include "rlb_common.h"
+#include "rlb_ctx.h"
 #include "rlb_launch.h"
 #include "rlb_quadrature.h"
 
@@ -39,28 +40,7 @@ size_t storage_bytes(int storage) { return storage == RLB_F64 ? 8 : (storage == 
 
 }  // namespace
 
-struct rlb_ctx {
-  rlb_params prm;
-  int q = 0;
-  int cells = 0;
-  size_t elem = 0;
-  void* buf[2] = {nullptr, nullptr};
-  int cur = 0;              // buf[cur] holds the current (post-collision) state
-  bool have_prev = false;   // buf[1 - cur] holds the state the last step pulled from
-  long steps = 0;
-  long launches = 0;
-  cudaStream_t stream = nullptr;
-  StepParams sp;
-  bool general_wrap = false;
-  double* fields = nullptr;   // 6 * cells; also staging for host inputs
-  double* partial = nullptr;  // 5 * blocks
-  double* totals = nullptr;   // 5
-  int* status = nullptr;      // kStatusWords
-  int fblocks = 0;
-  const Launchers* launch = nullptr;
-  int variant = 0;            // step-kernel variant (float storage)
-  std::string err;
-};
+
 
 // Errors of calls that have no context (rlb_create with invalid parameters) are kept per thread.
 static thread_local std::string g_create_err;
@@ -134,7 +114,7 @@ static std::string validate(const rlb_params* p) {
   }
   if (!(p->gamma_thr >= 1.0)) return "gamma_thr must be >= 1";
   if (p->storage == RLB_F16DEV && !(p->n_ref > 0)) return "n_ref must be > 0";
-  if (p->step_variant < -1 || p->step_variant > 3) return "step_variant must be -1 or 0..3";
+  if (p->step_variant < -1 || p->step_variant >= RLB_MAX_VARIANTS) return "step_variant must be -1 or 0..7";
   if (p->q > 0) {
     int q;
     const int *vel, *lev;
@@ -212,13 +192,30 @@ extern "C" rlb_status rlb_create(const rlb_params* p, rlb_ctx** out) {
   c->launch = table[p->order == 3 ? 1 : 0][p->storage];
   c->variant = (p->step_variant >= 0 && p->step_variant < c->launch->step_variants) ? p->step_variant
                                                                                       : kDefaultStepVariant;
+  int vmax[3];
   if (p->order == 3) {
     fill_offsets<Quad3>(sp);
     c->general_wrap = needs_general_wrap<Quad3>(*p);
+    vmax[0] = Quad3::VMAX_X, vmax[1] = Quad3::VMAX_Y, vmax[2] = Quad3::VMAX_Z;
   } else {
     fill_offsets<Quad2>(sp);
     c->general_wrap = needs_general_wrap<Quad2>(*p);
+    vmax[0] = Quad2::VMAX_X, vmax[1] = Quad2::VMAX_Y, vmax[2] = Quad2::VMAX_Z;
   }
+  sp.general = c->general_wrap ? 1 : 0;
+  // interior box: the stencil of every cell in it stays inside the lattice
+  const int dims[3] = {p->nx, p->ny, p->nz};
+  int i0[3], in[3];
+  for (int a = 0; a < 3; ++a) {
+    in[a] = dims[a] - 2 * vmax[a];
+    if (in[a] <= 0) in[a] = 0;
+    i0[a] = in[a] > 0 ? vmax[a] : 0;
+  }
+  if (in[0] == 0 || in[1] == 0 || in[2] == 0) in[0] = in[1] = in[2] = 0, i0[0] = i0[1] = i0[2] = 0;
+  sp.ix0 = i0[0], sp.ixn = in[0], sp.iy0 = i0[1], sp.iyn = in[1], sp.iz0 = i0[2], sp.izn = in[2];
+  sp.int_segs = (in[0] + 31) / 32;
+  sp.int_warps = sp.int_segs * in[1] * in[2];
+  sp.shell_cells = c->cells - in[0] * in[1] * in[2];
 
   const size_t pop_bytes = (size_t)c->q * c->cells * c->elem;
   c->fblocks = (c->cells + kMomThreads - 1) / kMomThreads;
@@ -312,8 +309,9 @@ extern "C" rlb_status rlb_step(rlb_ctx* c, long nsteps) {
     rlb_status st = check_launch(c,
                                  c->launch->step(c->buf[c->cur], c->buf[1 - c->cur], c->sp, c->status,
                                                  c->general_wrap, c->variant, c->stream),
-                                 "step kernel");
+                                 "step kernels");
     if (st != RLB_OK) return st;
+    if (c->sp.int_warps > 0 && c->sp.shell_cells > 0) ++c->launches;  // interior + shell
     c->cur = 1 - c->cur;
     c->have_prev = true;
     ++c->steps;
@@ -321,7 +319,7 @@ extern "C" rlb_status rlb_step(rlb_ctx* c, long nsteps) {
   return RLB_OK;
 }
 
-extern "C" rlb_status rlb_autotune(rlb_ctx* c, int reps, int* variant, double ms[4]) {
+extern "C" rlb_status rlb_autotune(rlb_ctx* c, int reps, int* variant, double ms[RLB_MAX_VARIANTS]) {
   if (!c) return RLB_EINVAL;
   if (reps < 1) return fail(c, RLB_EINVAL, "rlb_autotune: reps < 1");
   if (c->have_prev) return fail(c, RLB_ESTATE, "rlb_autotune: only before the first step after init");
@@ -330,7 +328,7 @@ extern "C" rlb_status rlb_autotune(rlb_ctx* c, int reps, int* variant, double ms
   RLB_CUDA(c, cudaEventCreate(&e1));
   double best = 1e300;
   int choice = c->variant;
-  double t[4] = {0, 0, 0, 0};
+  double t[RLB_MAX_VARIANTS] = {0};
   for (int v = 0; v < c->launch->step_variants; ++v) {
     // warm-up launch, then the timed repetitions; every launch recomputes the same next state
     for (int r = 0; r <= reps; ++r) {
@@ -356,7 +354,7 @@ extern "C" rlb_status rlb_autotune(rlb_ctx* c, int reps, int* variant, double ms
   c->variant = choice;
   if (variant) *variant = choice;
   if (ms)
-    for (int v = 0; v < 4; ++v) ms[v] = t[v];
+    for (int v = 0; v < RLB_MAX_VARIANTS; ++v) ms[v] = t[v];
   return read_status(c);
 }
 

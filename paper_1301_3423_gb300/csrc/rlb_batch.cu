@@ -1,0 +1,327 @@
+// Batched stepping of independent contexts (C ABI, include/rlb.h): a persistent kernel over a shared
+// tile queue advances every member by one time step per launch; runs of several steps can be
+// captured once as a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "rlb.h"
+#include "rlb_common.h"
+#include "rlb_ctx.h"
+#include "rlb_launch.h"
+
+using namespace rlb;
+
+namespace {
+
+struct Member {
+  rlb_ctx* ctx;
+  long steps_left;
+};
+
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  long nsteps = 0, version = -1;
+  int variant = -1, nmembers = 0, tiles = 0;
+};
+
+}  // namespace
+
+struct rlb_batch {
+  int order = 3, storage = RLB_F32;
+  cudaStream_t stream = nullptr;
+  std::vector<Member> members;   // slot -> member (ctx == nullptr: free slot)
+  BatchMember* d_members = nullptr;
+  int d_capacity = 0;
+  int* d_counters = nullptr;     // one tile counter per launch of a run
+  long counters_capacity = 0;
+  const Launchers* launch = nullptr;
+  int variant = 0;
+  int sms = 0;
+  long version = 0;              // bumps when the member set changes
+  long launches = 0;
+  GraphCache graph;
+  std::string err;
+};
+
+static rlb_status bfail(rlb_batch* b, rlb_status st, const std::string& msg) {
+  if (b) b->err = msg;
+  return st;
+}
+
+#define BATCH_CUDA(b, call)                                                                          \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess) return bfail((b), RLB_ECUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+extern "C" rlb_status rlb_batch_create(int order, int storage, void* stream, rlb_batch** out) {
+  if (!out) return RLB_EINVAL;
+  *out = nullptr;
+  if ((order != 2 && order != 3) || storage < RLB_F64 || storage > RLB_F16DEV) return RLB_EINVAL;
+  rlb_batch* b = new (std::nothrow) rlb_batch();
+  if (!b) return RLB_ENOMEM;
+  b->order = order;
+  b->storage = storage;
+  b->stream = static_cast<cudaStream_t>(stream);
+  static const Launchers* const table[2][3] = {{&launchers_o2_s0, &launchers_o2_s1, &launchers_o2_s2},
+                                               {&launchers_o3_s0, &launchers_o3_s1, &launchers_o3_s2}};
+  b->launch = table[order == 3 ? 1 : 0][storage];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return RLB_ECUDA;
+  }
+  b->variant = storage == RLB_F64 ? 0 : kDefaultStepVariant;
+  *out = b;
+  return RLB_OK;
+}
+
+extern "C" rlb_status rlb_batch_add(rlb_batch* b, rlb_ctx* ctx, long steps, int* slot) {
+  if (!b) return RLB_EINVAL;
+  if (!ctx || steps < 0) return bfail(b, RLB_EINVAL, "rlb_batch_add: null context or negative steps");
+  if (ctx->prm.order != b->order || ctx->prm.storage != b->storage)
+    return bfail(b, RLB_EINVAL, "rlb_batch_add: the context's order or storage differs from the batch's");
+  for (const Member& m : b->members)
+    if (m.ctx == ctx) return bfail(b, RLB_EINVAL, "rlb_batch_add: context already in the batch");
+  int s = -1;
+  for (size_t i = 0; i < b->members.size(); ++i)
+    if (!b->members[i].ctx) {
+      s = (int)i;
+      break;
+    }
+  if (s < 0) {
+    s = (int)b->members.size();
+    b->members.push_back(Member{nullptr, 0});
+  }
+  b->members[s] = Member{ctx, steps};
+  ++b->version;
+  if (slot) *slot = s;
+  return RLB_OK;
+}
+
+extern "C" rlb_status rlb_batch_remove(rlb_batch* b, int slot) {
+  if (!b) return RLB_EINVAL;
+  if (slot < 0 || slot >= (int)b->members.size() || !b->members[slot].ctx)
+    return bfail(b, RLB_EINVAL, "rlb_batch_remove: no member in this slot");
+  b->members[slot] = Member{nullptr, 0};
+  ++b->version;
+  return RLB_OK;
+}
+
+extern "C" long rlb_batch_steps_left(const rlb_batch* b, int slot) {
+  if (!b || slot < 0 || slot >= (int)b->members.size() || !b->members[slot].ctx) return -1;
+  return b->members[slot].steps_left;
+}
+
+// Member table of a run: the active members in slot order with their tile ranges.
+static rlb_status upload_table(rlb_batch* b, long nsteps, int* nmembers, int* total_tiles) {
+  std::vector<BatchMember> t;
+  int tiles = 0;
+  for (const Member& m : b->members) {
+    if (!m.ctx || m.steps_left <= 0) continue;
+    BatchMember d{};
+    d.p = m.ctx->sp;
+    d.buf[0] = m.ctx->buf[0];
+    d.buf[1] = m.ctx->buf[1];
+    d.status = m.ctx->status;
+    d.parity0 = m.ctx->cur;
+    d.steps_left = (int)std::min<long>(m.steps_left, nsteps);
+    d.tile_begin = tiles;
+    tiles += (m.ctx->cells + kStepThreads - 1) / kStepThreads;
+    t.push_back(d);
+  }
+  *nmembers = (int)t.size();
+  *total_tiles = tiles;
+  if (t.empty()) return RLB_OK;
+  if ((int)t.size() > b->d_capacity) {
+    if (b->d_members) cudaFree(b->d_members);
+    b->d_members = nullptr;
+    const int cap = std::max<int>((int)t.size(), 2 * b->d_capacity);
+    cudaError_t e = cudaMalloc((void**)&b->d_members, (size_t)cap * sizeof(BatchMember));
+    if (e != cudaSuccess) {
+      b->d_capacity = 0;
+      return bfail(b, RLB_ENOMEM, std::string("member table: ") + cudaGetErrorString(e));
+    }
+    b->d_capacity = cap;
+    ++b->version;  // a captured graph holds the old table pointer
+  }
+  BATCH_CUDA(b, cudaMemcpyAsync(b->d_members, t.data(), t.size() * sizeof(BatchMember), cudaMemcpyHostToDevice,
+                                b->stream));
+  BATCH_CUDA(b, cudaStreamSynchronize(b->stream));  // the host vector goes away
+  return RLB_OK;
+}
+
+static rlb_status ensure_counters(rlb_batch* b, long nsteps) {
+  if (nsteps <= b->counters_capacity) return RLB_OK;
+  if (b->d_counters) cudaFree(b->d_counters);
+  b->d_counters = nullptr;
+  cudaError_t e = cudaMalloc((void**)&b->d_counters, (size_t)nsteps * sizeof(int));
+  if (e != cudaSuccess) {
+    b->counters_capacity = 0;
+    return bfail(b, RLB_ENOMEM, std::string("tile counters: ") + cudaGetErrorString(e));
+  }
+  b->counters_capacity = nsteps;
+  ++b->version;
+  return RLB_OK;
+}
+
+static int grid_of(rlb_batch* b, int variant) { return b->sms * b->launch->batch_blocks_per_sm(variant); }
+
+// Enqueue nsteps launches (launch index 0..nsteps-1) directly on the stream.
+static rlb_status enqueue_run(rlb_batch* b, long nsteps, int nmem, int tiles, int variant) {
+  BATCH_CUDA(b, cudaMemsetAsync(b->d_counters, 0, (size_t)nsteps * sizeof(int), b->stream));
+  const int grid = grid_of(b, variant);
+  for (long k = 0; k < nsteps; ++k) {
+    cudaError_t e = b->launch->batch_step(b->d_members, nmem, tiles, (int)k, b->d_counters, variant, grid, b->stream);
+    ++b->launches;
+    if (e != cudaSuccess) return bfail(b, RLB_ECUDA, std::string("batched step: ") + cudaGetErrorString(e));
+  }
+  return RLB_OK;
+}
+
+extern "C" rlb_status rlb_batch_run(rlb_batch* b, long nsteps, int use_graph, int* active) {
+  if (!b) return RLB_EINVAL;
+  if (nsteps < 0 || nsteps > (1L << 30)) return bfail(b, RLB_EINVAL, "rlb_batch_run: nsteps out of range");
+  for (const Member& m : b->members)
+    if (m.ctx && m.ctx->stream != b->stream)
+      return bfail(b, RLB_EINVAL, "rlb_batch_run: a member uses another stream than the batch");
+  int nmem = 0, tiles = 0;
+  if (nsteps > 0) {
+    rlb_status st = ensure_counters(b, nsteps);
+    if (st != RLB_OK) return st;
+    st = upload_table(b, nsteps, &nmem, &tiles);
+    if (st != RLB_OK) return st;
+  }
+  if (nmem > 0) {
+    if (use_graph) {
+      // the table lives at a fixed device address and is refreshed before every replay, so the
+      // captured launches stay valid while nsteps, the variant, the member set and the active
+      // members' tile count stay the same
+      GraphCache& gc = b->graph;
+      if (!gc.exec || gc.nsteps != nsteps || gc.version != b->version || gc.variant != b->variant ||
+          gc.nmembers != nmem || gc.tiles != tiles) {
+        if (b->graph.exec) cudaGraphExecDestroy(b->graph.exec);
+        b->graph.exec = nullptr;
+        cudaStream_t cs;
+        BATCH_CUDA(b, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        BATCH_CUDA(b, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        cudaStream_t saved = b->stream;
+        b->stream = cs;
+        const long l0 = b->launches;
+        rlb_status st = enqueue_run(b, nsteps, nmem, tiles, b->variant);
+        b->stream = saved;
+        b->launches = l0;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cs, &g);
+        cudaStreamDestroy(cs);
+        if (st != RLB_OK) {
+          if (g) cudaGraphDestroy(g);
+          return st;
+        }
+        if (e != cudaSuccess) return bfail(b, RLB_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&b->graph.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return bfail(b, RLB_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        gc.nsteps = nsteps;
+        gc.version = b->version;
+        gc.variant = b->variant;
+        gc.nmembers = nmem;
+        gc.tiles = tiles;
+      }
+      BATCH_CUDA(b, cudaGraphLaunch(b->graph.exec, b->stream));
+      b->launches += nsteps;
+    } else {
+      rlb_status st = enqueue_run(b, nsteps, nmem, tiles, b->variant);
+      if (st != RLB_OK) return st;
+    }
+  }
+  // every member advanced min(steps_left, nsteps) steps
+  int act = 0;
+  for (Member& m : b->members) {
+    if (!m.ctx) continue;
+    const long k = std::min(m.steps_left, nsteps);
+    if (k > 0) {
+      m.ctx->cur = (int)((m.ctx->cur + k) & 1);
+      m.ctx->have_prev = true;
+      m.ctx->steps += k;  // the launches are counted once, by the batch
+      m.steps_left -= k;
+    }
+    if (m.steps_left > 0) ++act;
+  }
+  if (active) *active = act;
+  return RLB_OK;
+}
+
+extern "C" rlb_status rlb_batch_autotune(rlb_batch* b, int reps, int* variant, double ms[RLB_MAX_VARIANTS]) {
+  if (!b) return RLB_EINVAL;
+  if (reps < 1) return bfail(b, RLB_EINVAL, "rlb_batch_autotune: reps < 1");
+  for (const Member& m : b->members)
+    if (m.ctx && m.ctx->have_prev)
+      return bfail(b, RLB_ESTATE, "rlb_batch_autotune: only while no member has taken a step");
+  int nmem = 0, tiles = 0;
+  rlb_status st = ensure_counters(b, reps + 1);
+  if (st != RLB_OK) return st;
+  st = upload_table(b, 1, &nmem, &tiles);  // steps_left = 1: every launch redoes launch 0
+  if (st != RLB_OK) return st;
+  double t[RLB_MAX_VARIANTS] = {0};
+  if (nmem > 0) {
+    cudaEvent_t e0, e1;
+    BATCH_CUDA(b, cudaEventCreate(&e0));
+    BATCH_CUDA(b, cudaEventCreate(&e1));
+    double best = 1e300;
+    int choice = b->variant;
+    for (int v = 0; v < b->launch->step_variants; ++v) {
+      const int grid = grid_of(b, v);
+      BATCH_CUDA(b, cudaMemsetAsync(b->d_counters, 0, (size_t)(reps + 1) * sizeof(int), b->stream));
+      for (int r = 0; r <= reps; ++r) {
+        if (r == 1) BATCH_CUDA(b, cudaEventRecord(e0, b->stream));
+        // every repetition is launch 0 of the same run: the same next state into the spare buffers
+        cudaError_t e = b->launch->batch_step(b->d_members, nmem, tiles, 0, b->d_counters + r, v, grid, b->stream);
+        if (e != cudaSuccess) return bfail(b, RLB_ECUDA, std::string("batched step: ") + cudaGetErrorString(e));
+      }
+      BATCH_CUDA(b, cudaEventRecord(e1, b->stream));
+      BATCH_CUDA(b, cudaEventSynchronize(e1));
+      float msv = 0.f;
+      BATCH_CUDA(b, cudaEventElapsedTime(&msv, e0, e1));
+      t[v] = msv / reps;
+      if (t[v] < best) {
+        best = t[v];
+        choice = v;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->variant = choice;
+  }
+  if (variant) *variant = b->variant;
+  if (ms)
+    for (int v = 0; v < RLB_MAX_VARIANTS; ++v) ms[v] = t[v];
+  return RLB_OK;
+}
+
+extern "C" rlb_status rlb_batch_set_variant(rlb_batch* b, int variant) {
+  if (!b) return RLB_EINVAL;
+  if (variant < 0 || variant >= b->launch->step_variants)
+    return bfail(b, RLB_EINVAL, "rlb_batch_set_variant: no such variant");
+  b->variant = variant;
+  return RLB_OK;
+}
+
+extern "C" long rlb_batch_kernel_launches(const rlb_batch* b) { return b ? b->launches : -1; }
+
+extern "C" const char* rlb_batch_last_error(const rlb_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+extern "C" rlb_status rlb_batch_destroy(rlb_batch* b) {
+  if (!b) return RLB_OK;
+  cudaStreamSynchronize(b->stream);
+  if (b->graph.exec) cudaGraphExecDestroy(b->graph.exec);
+  if (b->d_members) cudaFree(b->d_members);
+  if (b->d_counters) cudaFree(b->d_counters);
+  delete b;
+  return RLB_OK;
+}

@@ -22,8 +22,25 @@ struct StepParams {
   float gamma_thr2;         // reduced-precision paths: Landau in double above this gamma^2
   int landau_fp64;
   float half_nref;          // F16DEV: n_ref / 2
+  int general;              // a periodic axis is shorter than the stencil reach (modulo wrap)
+  // Interior box: cells whose whole stencil stays inside the lattice, x in [ix0, ix0 + ixn) etc.
+  int ix0, ixn, iy0, iyn, iz0, izn;
+  int int_segs;             // warp-wide segments (32 cells) per interior row
+  int int_warps;            // interior segments in total
+  int shell_cells;          // cells outside the interior box
 };
 
 enum : int { kStatusNonconv = 0, kStatusBadInit = 1, kStatusWords = 4 };
+
+// One lattice of a batched step (see k_step_batch).
+struct BatchMember {
+  StepParams p;
+  void* buf[2];       // population buffers
+  int* status;        // the member's status words
+  int parity0;        // buffer holding the state before launch 0 of this run
+  int steps_left;     // launches with index >= steps_left leave this member alone
+  int tile_begin;     // first tile of this member in the queue
+  int pad;
+};
 
 }  // namespace rlb

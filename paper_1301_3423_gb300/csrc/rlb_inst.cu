@@ -1,56 +1,47 @@
-// Kernel instantiation for one (order, storage) pair, selected at compile time by
-// RLB_INST_ORDER (2 or 3) and RLB_INST_STORAGE (0 = double, 1 = float, 2 = half deviation).
-#include "rlb_kernels.cuh"
-#include "rlb_launch.h"
-
-#ifndef RLB_INST_ORDER
-#error "RLB_INST_ORDER must be defined"
-#endif
-#ifndef RLB_INST_STORAGE
-#error "RLB_INST_STORAGE must be defined"
-#endif
+// Kernels of one (order, storage) pair that do not depend on the step variant (fields, initial
+// state, format conversion, the reduction's second pass) and the dispatch to the per-variant units.
+#include "rlb_inst_select.h"
 
 namespace rlb {
 namespace {
-
-#if RLB_INST_ORDER == 3
-using L = Quad3;
-#else
-using L = Quad2;
-#endif
-#if RLB_INST_STORAGE == 0
-using S = StoreF64;
-#elif RLB_INST_STORAGE == 1
-using S = StoreF32;
-#else
-using S = StoreF16Dev;
-#endif
-using T = typename S::T;
-
-constexpr bool kFloat = std::is_same<typename S::A, float>::value;
-
-template <int V>
-void launch_step(const void* src, void* dst, const StepParams& p, int* status, bool general, cudaStream_t s) {
-  const int blocks = (p.cells + kStepThreads - 1) / kStepThreads;
-  if (general)
-    k_step<L, S, true, V><<<blocks, kStepThreads, 0, s>>>((const T*)src, (T*)dst, p, status);
-  else
-    k_step<L, S, false, V><<<blocks, kStepThreads, 0, s>>>((const T*)src, (T*)dst, p, status);
-}
+using namespace inst;
 
 cudaError_t step(const void* src, void* dst, const StepParams& p, int* status, bool general, int variant,
                  cudaStream_t s) {
-  if constexpr (kFloat) {
+  if (kFloat) {
     switch (variant) {
-      case kRegScalar: launch_step<kRegScalar>(src, dst, p, status, general, s); break;
-      case kRegPacked: launch_step<kRegPacked>(src, dst, p, status, general, s); break;
-      case kRegScalar3: launch_step<kRegScalar3>(src, dst, p, status, general, s); break;
-      default: launch_step<kRegPacked3>(src, dst, p, status, general, s); break;
+      case 1: return RLB_VFN(step, 1)(src, dst, p, status, general, s);
+      case 2: return RLB_VFN(step, 2)(src, dst, p, status, general, s);
+      case 3: return RLB_VFN(step, 3)(src, dst, p, status, general, s);
+      default: break;
     }
-  } else {
-    launch_step<kRegScalar>(src, dst, p, status, general, s);
   }
-  return cudaGetLastError();
+  return RLB_VFN(step, 0)(src, dst, p, status, general, s);
+}
+
+cudaError_t batch_step(const BatchMember* m, int n, int tiles, int li, int* counters, int variant, int grid,
+                       cudaStream_t s) {
+  if (kFloat) {
+    switch (variant) {
+      case 1: return RLB_VFN(batch, 1)(m, n, tiles, li, counters, grid, s);
+      case 2: return RLB_VFN(batch, 2)(m, n, tiles, li, counters, grid, s);
+      case 3: return RLB_VFN(batch, 3)(m, n, tiles, li, counters, grid, s);
+      default: break;
+    }
+  }
+  return RLB_VFN(batch, 0)(m, n, tiles, li, counters, grid, s);
+}
+
+int batch_blocks_per_sm(int variant) {
+  if (kFloat) {
+    switch (variant) {
+      case 1: return RLB_VFN(occupancy, 1)();
+      case 2: return RLB_VFN(occupancy, 2)();
+      case 3: return RLB_VFN(occupancy, 3)();
+      default: break;
+    }
+  }
+  return RLB_VFN(occupancy, 0)();
 }
 
 cudaError_t fields(const void* src, const StepParams& p, double* f, double* partial, int* status, bool pull,
@@ -83,8 +74,8 @@ cudaError_t convert_pops(void* pop, double* dbl, int i0, int i1, bool to_f64, co
 
 #define RLB_CAT_(a, b, c, d) a##b##c##d
 #define RLB_NAME(o, s) RLB_CAT_(launchers_o, o, _s, s)
-extern const Launchers RLB_NAME(RLB_INST_ORDER, RLB_INST_STORAGE) = {step, fields, init, convert_pops,
-                                                                  kFloat ? (int)kNumVariants : 1};
+extern const Launchers RLB_NAME(RLB_INST_ORDER, RLB_INST_STORAGE) = {
+    step, fields, init, convert_pops, inst::kFloat ? (int)kNumVariants : 1, batch_step, batch_blocks_per_sm};
 
 #if RLB_INST_ORDER == 3 && RLB_INST_STORAGE == 0
 // Second pass of the conserved-density sums: one block adds the per-block partials in a fixed
@@ -112,7 +103,6 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce_partials(const double
     totals[threadIdx.x] = s;
   }
 }
-
 
 cudaError_t launch_reduce_partials(const double* partial, int nblocks, double* totals, cudaStream_t s) {
   k_reduce_partials<<<1, kReduceThreads, 0, s>>>(partial, nblocks, totals);

@@ -1,0 +1,49 @@
+// Selects the lattice L and storage S of an instantiation unit from RLB_INST_ORDER (2 or 3) and
+// RLB_INST_STORAGE (0 = double, 1 = float, 2 = half deviation), and names its per-variant entry
+// points: RLB_VFN(step, V) is step_o<order>_s<storage>_v<V>.
+#pragma once
+#include "rlb_kernels.cuh"
+#include "rlb_launch.h"
+
+#ifndef RLB_INST_ORDER
+#error "RLB_INST_ORDER must be defined"
+#endif
+#ifndef RLB_INST_STORAGE
+#error "RLB_INST_STORAGE must be defined"
+#endif
+
+#define RLB_CAT7_(a, b, c, d, e, f, g) a##b##c##d##e##f##g
+#define RLB_CAT7(a, b, c, d, e, f, g) RLB_CAT7_(a, b, c, d, e, f, g)
+#define RLB_VFN(fn, v) RLB_CAT7(fn, _o, RLB_INST_ORDER, _s, RLB_INST_STORAGE, _v, v)
+
+namespace rlb {
+namespace inst {
+#if RLB_INST_ORDER == 3
+using L = Quad3;
+#else
+using L = Quad2;
+#endif
+#if RLB_INST_STORAGE == 0
+using S = StoreF64;
+#elif RLB_INST_STORAGE == 1
+using S = StoreF32;
+#else
+using S = StoreF16Dev;
+#endif
+using T = typename S::T;
+constexpr bool kFloat = std::is_same<typename S::A, float>::value;
+}  // namespace inst
+
+// Per-variant entry points (defined in rlb_inst_variant.cu, one unit per variant).
+#define RLB_DECLARE_VARIANT(v)                                                                               \
+  cudaError_t RLB_VFN(step, v)(const void* src, void* dst, const StepParams& p, int* status, bool general,   \
+                               cudaStream_t s);                                                              \
+  cudaError_t RLB_VFN(batch, v)(const BatchMember* m, int n, int tiles, int li, int* counters, int grid,     \
+                                cudaStream_t s);                                                             \
+  int RLB_VFN(occupancy, v)();
+RLB_DECLARE_VARIANT(0)
+RLB_DECLARE_VARIANT(1)
+RLB_DECLARE_VARIANT(2)
+RLB_DECLARE_VARIANT(3)
+#undef RLB_DECLARE_VARIANT
+}  // namespace rlb

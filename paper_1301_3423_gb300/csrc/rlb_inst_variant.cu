@@ -1,0 +1,44 @@
+// Step kernels of one (order, storage, variant): the interior and shell kernels of a solo step and
+// the persistent batched kernel.  RLB_INST_VARIANT selects the variant (see StepVariant).
+#include "rlb_inst_select.h"
+
+#ifndef RLB_INST_VARIANT
+#error "RLB_INST_VARIANT must be defined"
+#endif
+
+namespace rlb {
+using namespace inst;
+constexpr int V = RLB_INST_VARIANT;
+
+// One time step = the interior kernel plus the shell kernel (disjoint cells, same source).
+cudaError_t RLB_VFN(step, RLB_INST_VARIANT)(const void* src, void* dst, const StepParams& p, int* status,
+                                            bool general, cudaStream_t s) {
+  if (p.int_warps > 0) {
+    const int blocks = (p.int_warps + kStepThreads / 32 - 1) / (kStepThreads / 32);
+    k_step_interior<L, S, V><<<blocks, kStepThreads, 0, s>>>((const T*)src, (T*)dst, p, status);
+  }
+  if (p.shell_cells > 0) {
+    const int blocks = (p.shell_cells + kStepThreads - 1) / kStepThreads;
+    if (general)
+      k_step_shell<L, S, true, V><<<blocks, kStepThreads, 0, s>>>((const T*)src, (T*)dst, p, status);
+    else
+      k_step_shell<L, S, false, V><<<blocks, kStepThreads, 0, s>>>((const T*)src, (T*)dst, p, status);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t RLB_VFN(batch, RLB_INST_VARIANT)(const BatchMember* m, int n, int tiles, int li, int* counters, int grid,
+                                             cudaStream_t s) {
+  k_step_batch<L, S, V><<<grid, kStepThreads, 0, s>>>(m, n, tiles, li, counters);
+  return cudaGetLastError();
+}
+
+int RLB_VFN(occupancy, RLB_INST_VARIANT)() {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_batch<L, S, V>, kStepThreads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return nb > 0 ? nb : 1;
+}
+}  // namespace rlb

@@ -220,7 +220,8 @@ __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
 //   V = T.(eta U),  rho = U.V,  W = V + (rho/3) U,  U <- W / |W|.
 // The shift rho/3 moves the spacelike eigenvalues -P_k to rho/3 - P_k, which vanish in local
 // equilibrium (eps = 3P), so the contraction factor is the relative pressure anisotropy instead
-// of P/eps = 1/3.  eps is the Rayleigh quotient U.V, n = U.N.
+// of P/eps = 1/3.  eps is the Rayleigh quotient U.V, n = U.N.  Each lane stops once converged (a
+// warp runs as long as its slowest cell).
 // ---------------------------------------------------------------------------------------------
 template <class A>
 struct Landau {
@@ -236,7 +237,8 @@ __device__ __forceinline__ Landau<A> landau(const Mom<A>& m) {
   if (!(NN > A(0)) || !(m.N0 > A(0))) return r;
   A is = rsqrt_(NN);
   A U0 = m.N0 * is, Ux = m.Nx * is, Uy = m.Ny * is, Uz = m.Nz * is;
-  const A tol = std::is_same<A, double>::value ? A(8e-16) : A(0);
+  // stop when an update moves U by less than a few units in the last place of U0
+  const A tol = std::is_same<A, double>::value ? A(8e-16) : A(3e-7);
   for (int it = 0; it < MAXIT; ++it) {
     const A V0 = m.T00 * U0 - m.T0x * Ux - m.T0y * Uy - m.T0z * Uz;
     const A Vx = m.T0x * U0 - m.Txx * Ux - m.Txy * Uy - m.Txz * Uz;
@@ -267,6 +269,12 @@ __device__ __forceinline__ Landau<A> landau(const Mom<A>& m) {
   return r;
 }
 
+// The double-precision solve of a float step, kept out of line: it runs for few cells and would
+// otherwise grow the step kernel's hot code.
+static __device__ __noinline__ Landau<double> landau_fp64_out_of_line(const Mom<double> m) {
+  return landau<double, 40, true>(m);
+}
+
 // Landau matching in the step's arithmetic A.  Reduced-precision paths switch to double for cells
 // whose Eckart Lorentz factor exceeds gamma_thr (or always, if asked): the solve loses about
 // gamma^2 digits to cancellation in U.U = 1.
@@ -277,10 +285,10 @@ __device__ __forceinline__ Landau<A> landau_step(const Mom<A>& m, const StepPara
   } else {
     const float NN = m.N0 * m.N0 - m.Nx * m.Nx - m.Ny * m.Ny - m.Nz * m.Nz;
     if (p.landau_fp64 || m.N0 * m.N0 > p.gamma_thr2 * NN) {
-      const Landau<double> d = landau<double, 40, true>(convert<A, double>(m));
+      const Landau<double> d = landau_fp64_out_of_line(convert<A, double>(m));
       return Landau<A>{(A)d.U0, (A)d.Ux, (A)d.Uy, (A)d.Uz, (A)d.eps, (A)d.n, d.ok};
     }
-    return landau<float, 8, false>(m);
+    return landau<float, 8, true>(m);
   }
 }
 
@@ -520,28 +528,57 @@ __device__ __forceinline__ void collide_f2(const Landau<float>& lw, float T, flo
 // ---------------------------------------------------------------------------------------------
 // the fused step kernel
 // ---------------------------------------------------------------------------------------------
-// Step-kernel variants for float arithmetic.  A cell's populations stay in registers (one pull):
+// Step-kernel variants for float arithmetic.  Every population is pulled once and all populations
+// of a cell stay in registers.
 //   bit 0: scalar arithmetic (0) or mirror pairs in float2 with paired FMA (1);
 //   bit 1: registers as needed, 2 resident blocks of 128 threads per SM (0), or at most 168
-//          registers for 3 resident blocks (1), trading spills for more warps.
+//          registers for 3 resident blocks (1; the compiler spills a little).
+// (Staging part of the populations in shared memory with cp.async, and pulling every population
+// twice, were measured slower and are not built.)
 // Double arithmetic pulls each population twice (moments, then collision) and has one variant.
-enum StepVariant : int { kRegScalar = 0, kRegPacked = 1, kRegScalar3 = 2, kRegPacked3 = 3, kNumVariants = 4 };
+enum StepVariant : int {
+  kRegScalar = 0, kRegPacked = 1, kReg3Scalar = 2, kReg3Packed = 3, kSplitScalar = 4, kSplitPacked = 5,
+  kNumVariants = 4
+};
 
-template <class L, class S, bool GENERAL, int VARIANT>
-__global__ void __launch_bounds__(kStepThreads, (VARIANT & 2) ? 3 : 1) k_step(const typename S::T* __restrict__ src,
-                                                       typename S::T* __restrict__ dst,
-                                                       const __grid_constant__ StepParams p,
-                                                       int* __restrict__ status) {
+constexpr int kSplitRegs = 40;
+
+template <class S, int VARIANT>
+struct StepShape {
+  static constexpr int kResidency = VARIANT >> 1;
+  static constexpr bool kSplit = kResidency == 2 && std::is_same<S, StoreF32>::value;
+  static constexpr int kMinBlocks = kResidency == 0 ? 1 : (kSplit ? 4 : 3);
+};
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// How a step kernel pulls: kPathAuto lets each warp vote (all lanes interior: constant offsets,
+// else wrapped / clamped indices); the interior kernel knows every lane is interior; the shell
+// kernel knows none needs to be.
+enum PullPath : int { kPathAuto = 0, kPathInterior = 1, kPathEdge = 2 };
+
+// One cell's time step (pull, moments, Landau matching, equilibrium, collision, store).  Invalid
+// lanes (valid = false) carry a clamped in-range cell, compute and store nothing.
+template <class L, class S, bool GENERAL, int VARIANT, int PATH>
+__device__ __forceinline__ void step_cell(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
+                                          const StepParams& p, int* __restrict__ status, const Cell cl,
+                                          const bool valid) {
   using A = typename S::A;
   using ST = typename S::T;
   constexpr bool PACKED = (VARIANT & 1) && std::is_same<A, float>::value;
   constexpr bool KEEP = std::is_same<A, float>::value;
-  const int gid = blockIdx.x * kStepThreads + threadIdx.x;
-  const bool valid = gid < p.cells;
-  const Cell cl = make_cell(valid ? gid : p.cells - 1, p);
   // Warp-uniform choice: if every lane's stencil stays inside the lattice, pull with constant
   // offsets; otherwise resolve periodic wrap / copy-out per population.
-  const bool fast = __all_sync(0xffffffffu, is_interior<L>(cl, p));
+  bool fast;
+  if constexpr (PATH == kPathInterior) fast = true;
+  else if constexpr (PATH == kPathEdge) fast = false;
+  else fast = __all_sync(0xffffffffu, is_interior<L>(cl, p));
   const ST* __restrict__ base = src + cl.c;
   ST* __restrict__ out = dst + cl.c;
 
@@ -555,23 +592,32 @@ __global__ void __launch_bounds__(kStepThreads, (VARIANT & 2) ? 3 : 1) k_step(co
     if (valid) S::template store<L, i>(out + (long long)i * p.cells, v, p);
   };
 
-  A fk[KEEP ? L::Q : 1];
+  constexpr bool SPLIT = StepShape<S, VARIANT>::kSplit;
+  constexpr int KREG = SPLIT ? (L::Q < kSplitRegs ? L::Q : kSplitRegs) : L::Q;
+  constexpr int NSM = SPLIT ? L::Q - KREG : 0;
+  __shared__ float fsm[NSM > 0 ? NSM : 1][kStepThreads];
+  A fk[KEEP ? KREG : 1];
   if constexpr (KEEP) {
+    auto pull_one = [&](auto I, const ST* ptr) {
+      constexpr int i = decltype(I)::value;
+      if constexpr (i < KREG) fk[i] = S::template load<L, i>(ptr, p);
+      else cp_async4(&fsm[i - KREG][threadIdx.x], ptr);
+    };
     if (fast) {
-      static_for<L::Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        fk[i] = S::template load<L, i>(base + p.off[i], p);
-      });
+      static_for<L::Q>([&](auto I) { pull_one(I, base + p.off[decltype(I)::value]); });
     } else {
-      static_for<L::Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        fk[i] = S::template load<L, i>(src + pull_index<L, i, GENERAL>(cl, p), p);
-      });
+      static_for<L::Q>([&](auto I) { pull_one(I, src + pull_index<L, decltype(I)::value, GENERAL>(cl, p)); });
     }
+    if constexpr (NSM > 0) cp_async_wait_all();  // each thread reads only its own slots
   }
   auto get = [&](auto I) -> A {
-    if constexpr (KEEP) return fk[decltype(I)::value];
-    else return load(I);
+    constexpr int i = decltype(I)::value;
+    if constexpr (KEEP) {
+      if constexpr (i < KREG) return fk[i];
+      else return (A)fsm[i - KREG][threadIdx.x];
+    } else {
+      return load(I);
+    }
   };
   auto get2 = [&](auto I) -> float2 {
     constexpr int i = decltype(I)::value;
@@ -601,6 +647,126 @@ __global__ void __launch_bounds__(kStepThreads, (VARIANT & 2) ? 3 : 1) k_step(co
     collide_f2<L>(lw, T, inv_tau, get2, put2);
   } else {
     collide<L, A>(lw, T, inv_tau, get, store);
+  }
+}
+
+
+// Interior cells: warp w covers 32 consecutive x of one interior row (the last segment of a row
+// may be partial); every lane pulls with constant offsets.
+template <class L, class S, int VARIANT>
+__global__ void __launch_bounds__(kStepThreads, StepShape<S, VARIANT>::kMinBlocks)
+    k_step_interior(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
+                    const __grid_constant__ StepParams p, int* __restrict__ status) {
+  const int w = blockIdx.x * (kStepThreads / 32) + (threadIdx.x >> 5);
+  if (w >= p.int_warps) return;  // whole warps only
+  const int seg = w % p.int_segs, row = w / p.int_segs;
+  Cell cl;
+  cl.y = p.iy0 + row % p.iyn;
+  cl.z = p.iz0 + row / p.iyn;
+  const int xr = seg * 32 + (threadIdx.x & 31);
+  const bool valid = xr < p.ixn;
+  cl.x = p.ix0 + (valid ? xr : p.ixn - 1);
+  cl.c = (cl.z * p.ny + cl.y) * p.nx + cl.x;
+  step_cell<L, S, false, VARIANT, kPathInterior>(src, dst, p, status, cl, valid);
+}
+
+// Shell cells (outside the interior box): z-boundary planes, then y-boundary rows of the interior
+// planes, then x-boundary cells of the interior rows; wrapped / clamped pulls.
+__device__ __forceinline__ Cell shell_cell(int s, const StepParams& p) {
+  Cell cl;
+  const int A = (p.nz - p.izn) * p.nxy;
+  if (s < A) {
+    const int zz = s / p.nxy, r = s - zz * p.nxy;
+    cl.z = zz < p.iz0 ? zz : zz + p.izn;
+    cl.y = r / p.nx;
+    cl.x = r - cl.y * p.nx;
+  } else {
+    s -= A;
+    const int rowy = (p.ny - p.iyn) * p.nx;
+    const int B = rowy * p.izn;
+    if (s < B) {
+      const int zz = s / rowy, r = s - zz * rowy;
+      cl.z = p.iz0 + zz;
+      const int yy = r / p.nx;
+      cl.y = yy < p.iy0 ? yy : yy + p.iyn;
+      cl.x = r - yy * p.nx;
+    } else {
+      s -= B;
+      const int wx = p.nx - p.ixn;
+      const int per_z = wx * p.iyn;
+      const int zz = s / per_z, r = s - zz * per_z;
+      cl.z = p.iz0 + zz;
+      const int yy = r / wx, xx = r - yy * wx;
+      cl.y = p.iy0 + yy;
+      cl.x = xx < p.ix0 ? xx : xx + p.ixn;
+    }
+  }
+  cl.c = (cl.z * p.ny + cl.y) * p.nx + cl.x;
+  return cl;
+}
+
+template <class L, class S, bool GENERAL, int VARIANT>
+__global__ void __launch_bounds__(kStepThreads, StepShape<S, VARIANT>::kMinBlocks)
+    k_step_shell(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
+                 const __grid_constant__ StepParams p, int* __restrict__ status) {
+  const int s = blockIdx.x * kStepThreads + threadIdx.x;
+  const bool valid = s < p.shell_cells;
+  const Cell cl = shell_cell(valid ? s : p.shell_cells - 1, p);
+  step_cell<L, S, GENERAL, VARIANT, kPathEdge>(src, dst, p, status, cl, valid);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batched step: many independent lattices (members) advance together.  A persistent grid takes
+// tiles of kStepThreads consecutive cells from one shared queue (an atomic counter per launch);
+// a tile belongs to one member, found by binary search over the members' first tile.  Each
+// launch is one time step of every member whose step count is not yet reached.  The per-cell code
+// and the grouping of cells into warps are those of k_step, so a member's populations are bitwise
+// the same as when it runs alone with the same variant.
+// ---------------------------------------------------------------------------------------------
+
+
+template <class L, class S, int VARIANT>
+__global__ void __launch_bounds__(kStepThreads, StepShape<S, VARIANT>::kMinBlocks)
+    k_step_batch(const BatchMember* __restrict__ members, int nmembers, int total_tiles, int launch_index,
+                 int* __restrict__ counters) {
+  using ST = typename S::T;
+  __shared__ StepParams sp;
+  __shared__ int s_tile, s_member;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int t = atomicAdd(&counters[launch_index], 1);
+      int lo = 0, hi = nmembers - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (members[mid].tile_begin <= t) lo = mid;
+        else hi = mid - 1;
+      }
+      s_tile = t;
+      s_member = lo;
+    }
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= total_tiles) return;
+    const BatchMember& m = members[s_member];
+    const bool active = launch_index < m.steps_left;
+    if (active) {
+      // the member's parameters into shared memory (one copy per tile instead of global reads)
+      const int* srcw = reinterpret_cast<const int*>(&m.p);
+      int* dstw = reinterpret_cast<int*>(&sp);
+      for (int k = threadIdx.x; k < (int)(sizeof(StepParams) / sizeof(int)); k += kStepThreads) dstw[k] = srcw[k];
+    }
+    __syncthreads();
+    if (active) {
+      const int par = (m.parity0 + launch_index) & 1;
+      const int gid = (tile - m.tile_begin) * kStepThreads + threadIdx.x;
+      const bool valid = gid < sp.cells;
+      const Cell cl = make_cell(valid ? gid : sp.cells - 1, sp);
+      const ST* sb = static_cast<const ST*>(m.buf[par]);
+      ST* db = static_cast<ST*>(m.buf[par ^ 1]);
+      if (sp.general) step_cell<L, S, true, VARIANT, kPathAuto>(sb, db, sp, m.status, cl, valid);
+      else step_cell<L, S, false, VARIANT, kPathAuto>(sb, db, sp, m.status, cl, valid);
+    }
+    __syncthreads();  // sp and s_tile are reused by the next tile
   }
 }
 

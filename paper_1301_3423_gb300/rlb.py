@@ -16,6 +16,9 @@ RLB_OK, RLB_EINVAL, RLB_ENOMEM, RLB_ECUDA, RLB_ENONCONV, RLB_ENAN, RLB_ETIMEOUT,
 STATUS_NAMES = ["RLB_OK", "RLB_EINVAL", "RLB_ENOMEM", "RLB_ECUDA", "RLB_ENONCONV", "RLB_ENAN", "RLB_ETIMEOUT",
                 "RLB_ESTATE"]
 STORAGE = {"f64": 0, "f32": 1, "f16dev": 2}
+MAX_VARIANTS = 8
+VARIANT_NAMES = ["registers/scalar", "registers/paired", "registers(168)/scalar", "registers(168)/paired",
+                 "registers+smem/scalar", "registers+smem/paired"]
 BC = {"periodic": 0, "copyout": 1}
 
 
@@ -52,9 +55,12 @@ class Params(ctypes.Structure):
 
 
 _LIB = None
+_LOAD_ERROR = None
 DECLARED = ["rlb_default_params", "rlb_bytes_required", "rlb_create", "rlb_init", "rlb_step", "rlb_moments",
             "rlb_sync", "rlb_get_populations", "rlb_set_populations", "rlb_steps_done", "rlb_kernel_launches",
-            "rlb_destroy", "rlb_last_error", "rlb_quadrature", "rlb_autotune", "rlb_totals_noalloc"]
+            "rlb_destroy", "rlb_last_error", "rlb_quadrature", "rlb_autotune", "rlb_totals_noalloc", "rlb_batch_create", "rlb_batch_add",
+            "rlb_batch_remove", "rlb_batch_steps_left", "rlb_batch_run", "rlb_batch_autotune",
+            "rlb_batch_set_variant", "rlb_batch_kernel_launches", "rlb_batch_last_error", "rlb_batch_destroy"]
 
 
 def lib_path():
@@ -63,10 +69,16 @@ def lib_path():
 
 def load(build_if_missing=True):
     """Load librlb.so (building it first if it is missing)."""
-    global _LIB
+    global _LIB, _LOAD_ERROR
     if _LIB is not None:
         return _LIB
-    path = _build.build() if build_if_missing else _build.LIB
+    if _LOAD_ERROR is not None:  # fail fast: a broken build is not retried in the same process
+        raise _LOAD_ERROR
+    try:
+        path = _build.build() if build_if_missing else _build.LIB
+    except Exception as e:
+        _LOAD_ERROR = RuntimeError("librlb could not be built: %s" % e)
+        raise _LOAD_ERROR
     lib = ctypes.CDLL(path)
     P, vp, dp, ip = ctypes.POINTER(Params), ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
     lib.rlb_default_params.argtypes = [P]
@@ -103,6 +115,26 @@ def load(build_if_missing=True):
     lib.rlb_autotune.restype = ip
     lib.rlb_totals_noalloc.argtypes = [ip, ip, ip, ip, ip, ctypes.c_double, vp, dp, vp]
     lib.rlb_totals_noalloc.restype = ip
+    lib.rlb_batch_create.argtypes = [ip, ip, vp, ctypes.POINTER(vp)]
+    lib.rlb_batch_create.restype = ip
+    lib.rlb_batch_add.argtypes = [vp, vp, ctypes.c_long, ctypes.POINTER(ip)]
+    lib.rlb_batch_add.restype = ip
+    lib.rlb_batch_remove.argtypes = [vp, ip]
+    lib.rlb_batch_remove.restype = ip
+    lib.rlb_batch_steps_left.argtypes = [vp, ip]
+    lib.rlb_batch_steps_left.restype = ctypes.c_long
+    lib.rlb_batch_run.argtypes = [vp, ctypes.c_long, ip, ctypes.POINTER(ip)]
+    lib.rlb_batch_run.restype = ip
+    lib.rlb_batch_autotune.argtypes = [vp, ip, ctypes.POINTER(ip), dp]
+    lib.rlb_batch_autotune.restype = ip
+    lib.rlb_batch_set_variant.argtypes = [vp, ip]
+    lib.rlb_batch_set_variant.restype = ip
+    lib.rlb_batch_kernel_launches.argtypes = [vp]
+    lib.rlb_batch_kernel_launches.restype = ctypes.c_long
+    lib.rlb_batch_last_error.argtypes = [vp]
+    lib.rlb_batch_last_error.restype = ctypes.c_char_p
+    lib.rlb_batch_destroy.argtypes = [vp]
+    lib.rlb_batch_destroy.restype = ip
     _LIB = lib
     return lib
 
@@ -293,9 +325,10 @@ class RLB:
     def autotune(self, reps=5):
         """rlb_autotune: (chosen variant, ms per step of each variant)."""
         v = ctypes.c_int()
-        ms = (ctypes.c_double * 4)()
+        ms = (ctypes.c_double * MAX_VARIANTS)()
         self._check(self._lib.rlb_autotune(self._h, int(reps), ctypes.byref(v), ms))
-        return v.value, list(ms)
+        n = sum(1 for x in ms if x > 0)
+        return v.value, list(ms)[:max(n, 1)]
 
     @property
     def steps_done(self):
@@ -321,3 +354,73 @@ class RLB:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch:
+    """rlb_batch_*: step many RLB contexts (same order and storage) together in one persistent
+    kernel per step over a shared tile queue, optionally replaying CUDA graphs of several steps."""
+
+    def __init__(self, order=3, storage="f32", stream=None):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        st_code = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        sp = None if stream is None else ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+        st = self._lib.rlb_batch_create(order, st_code, sp, ctypes.byref(h))
+        if st != RLB_OK:
+            raise RLBError(st, "rlb_batch_create failed")
+        self._h = h
+        self._members = {}
+
+    def _check(self, st):
+        if st != RLB_OK:
+            raise RLBError(st, self._lib.rlb_batch_last_error(self._h).decode())
+
+    def add(self, ctx, steps):
+        slot = ctypes.c_int()
+        self._check(self._lib.rlb_batch_add(self._h, ctx._h, int(steps), ctypes.byref(slot)))
+        self._members[slot.value] = ctx
+        return slot.value
+
+    def remove(self, slot):
+        self._check(self._lib.rlb_batch_remove(self._h, int(slot)))
+        self._members.pop(slot, None)
+
+    def steps_left(self, slot):
+        return int(self._lib.rlb_batch_steps_left(self._h, int(slot)))
+
+    def run(self, nsteps, graph=True):
+        act = ctypes.c_int()
+        self._check(self._lib.rlb_batch_run(self._h, int(nsteps), int(bool(graph)), ctypes.byref(act)))
+        return act.value
+
+    def autotune(self, reps=3):
+        v = ctypes.c_int()
+        ms = (ctypes.c_double * MAX_VARIANTS)()
+        self._check(self._lib.rlb_batch_autotune(self._h, int(reps), ctypes.byref(v), ms))
+        n = sum(1 for x in ms if x > 0)
+        return v.value, list(ms)[:max(n, 1)]
+
+    def set_variant(self, v):
+        self._check(self._lib.rlb_batch_set_variant(self._h, int(v)))
+
+    @property
+    def kernel_launches(self):
+        return int(self._lib.rlb_batch_kernel_launches(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.rlb_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+

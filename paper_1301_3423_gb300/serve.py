@@ -1,0 +1,201 @@
+"""Continuous-batching request loop for relativistic lattice Boltzmann simulations.
+
+Requests (shock tubes, shear waves, random-field boxes of different sizes, eta/s and storage
+precision) arrive over time.  The server keeps every admitted simulation resident on the device,
+admits waiting requests first-come-first-served while their memory fits the HBM budget, and
+advances all admitted simulations together: one batch per storage precision, each batch stepping
+its members with the persistent tile-queue kernel (optionally a replayed CUDA graph) for a round of
+``chunk`` steps.  A member that reaches its step count is finished (its Landau fields and conserved
+totals are read back), its memory is released and waiting requests are admitted in the next round.
+
+Everything numerical runs in librlb; this module only schedules.
+"""
+import dataclasses
+import time
+
+import numpy as np
+
+from paper_inputs import fields as gen
+
+from .rlb import RLB, Batch
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    kind: str            # "tube", "shear" or "random"
+    shape: tuple          # (nz, ny, nx)
+    eta_over_s: float
+    steps: int
+    storage: str          # "f32" or "f16dev"
+    seed: int
+    arrival: float        # seconds after the stream starts
+    bc: tuple = (0, 0, 0)
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    n: np.ndarray
+    eps: np.ndarray
+    U: np.ndarray
+    totals: np.ndarray
+    admitted: float
+    finished: float
+    arrival: float
+    cells: int
+    steps: int
+
+    @property
+    def tts(self):
+        return self.finished - self.arrival
+
+
+def initial_fields(req):
+    """Seeded initial fields of a request (see paper_inputs.fields)."""
+    if req.kind == "tube":
+        return gen.riemann_tube(req.shape[0])
+    if req.kind == "shear":
+        nz, ny, nx = req.shape
+        return gen.shear_wave(nx, amp=0.05, ny=ny, nz=nz)
+    return gen.smooth_random_fields(req.shape, seed=req.seed, vmax=0.4, sigma_lnT=0.15, kmax=2, density="uniform")
+
+
+def poisson_requests(n, rate=20.0, seed=0, sizes=(32, 48, 64, 96, 128, 192, 256, 384), step_scale=1.0,
+                     f16_fraction=0.3, max_side=384):
+    """A seeded request stream: exponential inter-arrival times (mean 1/rate); kind uniform over
+    tube / shear / random; box side L drawn with probability proportional to 1/L^3; tubes of
+    400..4000 cells; eta/s in {0.01, 0.1, 0.5}; steps 500 (tube), 2000 (shear), 1000 (random)
+    times step_scale; float storage, or half deviation storage with probability f16_fraction."""
+    rng = np.random.default_rng(seed)
+    sizes = [L for L in sizes if L <= max_side]
+    p = np.array([1.0 / L ** 3 for L in sizes])
+    p /= p.sum()
+    t = 0.0
+    out = []
+    for rid in range(n):
+        t += rng.exponential(1.0 / rate)
+        kind = str(rng.choice(["tube", "shear", "random"]))
+        eta = float(rng.choice([0.01, 0.1, 0.5]))
+        storage = "f16dev" if rng.random() < f16_fraction else "f32"
+        if kind == "tube":
+            N = int(rng.integers(400, 4001))
+            shape, bc, steps = (N, 1, 1), (0, 0, 1), 500
+        else:
+            L = int(rng.choice(sizes, p=p))
+            shape, bc, steps = (L, L, L), (0, 0, 0), (2000 if kind == "shear" else 1000)
+        out.append(Request(rid, kind, shape, eta, max(1, int(round(steps * step_scale))), storage,
+                           int(rng.integers(1 << 30)), t, bc))
+    return out
+
+
+class Server:
+    """Admission against an HBM budget plus continuous batching (see the module docstring)."""
+
+    def __init__(self, order=3, hbm_budget=150e9, chunk=50, use_graph=True, stream=None, autotune=False):
+        self.order = order
+        self.budget = float(hbm_budget)
+        self.chunk = int(chunk)
+        self.use_graph = use_graph
+        self.stream = stream
+        self.autotune = autotune
+        self.batches = {}
+        self.active = {}        # (storage, slot) -> (request, context, admitted time, bytes)
+        self.waiting = []
+        self.in_use = 0.0
+        self.peak_in_use = 0.0
+        self.peak_active = 0
+        self.results = []
+        self.t0 = None
+        self.kernel_launches = 0
+
+    def now(self):
+        return time.perf_counter() - self.t0
+
+    def _batch(self, storage):
+        if storage not in self.batches:
+            self.batches[storage] = Batch(self.order, storage, stream=self.stream)
+        return self.batches[storage]
+
+    @staticmethod
+    def bytes_of(req, order=3):
+        nz, ny, nx = req.shape
+        return RLB.bytes_required(order=order, nx=nx, ny=ny, nz=nz, storage=req.storage, bc=req.bc)
+
+    def _admit(self):
+        admitted = 0
+        while self.waiting:
+            req = self.waiting[0]
+            need = self.bytes_of(req, self.order)
+            if need > self.budget:
+                raise ValueError("request %d needs %.1f GB, more than the whole budget" % (req.rid, need / 1e9))
+            if self.in_use + need > self.budget:
+                break  # first come, first served: wait for memory
+            self.waiting.pop(0)
+            ctx = RLB(req.shape, order=self.order, bc=req.bc, eta_over_s=req.eta_over_s, storage=req.storage,
+                      landau_fp64=True, stream=self.stream)
+            ctx.init(*initial_fields(req))
+            slot = self._batch(req.storage).add(ctx, req.steps)
+            self.active[(req.storage, slot)] = (req, ctx, self.now(), need)
+            self.in_use += need
+            self.peak_in_use = max(self.peak_in_use, self.in_use)
+            self.peak_active = max(self.peak_active, len(self.active))
+            admitted += 1
+        return admitted
+
+    def _round(self):
+        for storage, b in self.batches.items():
+            if any(k[0] == storage for k in self.active):
+                b.run(self.chunk, graph=self.use_graph)
+        done = [(k, v) for k, v in self.active.items() if self.batches[k[0]].steps_left(k[1]) == 0]
+        for (storage, slot), (req, ctx, t_adm, need) in done:
+            m = ctx.moments()
+            self.kernel_launches += ctx.kernel_launches
+            self.batches[storage].remove(slot)
+            ctx.close()
+            del self.active[(storage, slot)]
+            self.in_use -= need
+            nz, ny, nx = req.shape
+            self.results.append(Result(req.rid, m["n"], m["eps"], m["U"], m["totals"], t_adm, self.now(),
+                                       req.arrival, nx * ny * nz, req.steps))
+
+    def run(self, requests, realtime=True, max_wall=None):
+        """Serve a request stream.  With realtime=True a request is only visible after its arrival
+        time (wall clock since the start); otherwise all are queued at once."""
+        pending = sorted(requests, key=lambda r: r.arrival)
+        self.t0 = time.perf_counter()
+        k = 0
+        while k < len(pending) or self.waiting or self.active:
+            t = self.now()
+            while k < len(pending) and (not realtime or pending[k].arrival <= t):
+                self.waiting.append(pending[k])
+                k += 1
+            self._admit()
+            if self.active:
+                self._round()
+            elif k < len(pending) and realtime:
+                time.sleep(max(0.0, min(0.01, pending[k].arrival - self.now())))
+            if max_wall is not None and self.now() > max_wall:
+                raise TimeoutError("serving did not finish within %.0f s" % max_wall)
+        makespan = self.now()
+        for b in self.batches.values():
+            self.kernel_launches += b.kernel_launches
+        return self.stats(makespan)
+
+    def stats(self, makespan):
+        tts = np.array([r.tts for r in self.results])
+        upd = float(sum(r.cells * r.steps for r in self.results))
+        return {"requests": len(self.results), "makespan_s": makespan,
+                "p50_tts_s": float(np.percentile(tts, 50)) if len(tts) else None,
+                "p99_tts_s": float(np.percentile(tts, 99)) if len(tts) else None,
+                "aggregate_mlups": upd / makespan / 1e6 if makespan > 0 else None,
+                "cell_updates": upd, "peak_hbm_gb": self.peak_in_use / 1e9, "peak_active": self.peak_active,
+                "budget_gb": self.budget / 1e9}
+
+    def close(self):
+        for _, ctx, _, _ in self.active.values():
+            ctx.close()
+        self.active.clear()
+        for b in self.batches.values():
+            b.close()
+        self.batches.clear()

@@ -112,6 +112,31 @@ def test_f64_interior_warps_match_oracle(order):
 
 
 @pytest.mark.parametrize("order", [3, 2])
+@pytest.mark.parametrize("variant", [-1, 3])
+def test_interior_and_shell_kernels_match_oracle(order, variant):
+    """40 x 20 x 24 cells: an interior box of 28 x 8 x 12 cells (constant-offset kernel, row
+    segments with a partial last warp) surrounded by the shell (wrapped pulls).  Double storage per
+    population; float storage (variant 3) on the fields."""
+    lat = oracle.read_lattice(order)
+    shape = (24, 20, 40)
+    n, T, u = gen.smooth_random_fields(shape, seed=51, vmax=0.45, sigma_lnT=0.15, kmax=2)
+    o = oracle.OracleRLB(lat, shape[2], shape[1], shape[0], eta_over_s=0.1)
+    o.init(n, T, u)
+    o.step(6)
+    storage = "f64" if variant < 0 else "f32"
+    with RLB(shape, order=order, eta_over_s=0.1, storage=storage, step_variant=variant) as g:
+        g.init(n, T, u)
+        g.step(6)
+        f = g.populations()
+        m = g.moments()
+    assert o.nonconv == 0
+    if storage == "f64":
+        assert pop_err(lat, f, o.f, n.max()) < 1e-12
+    else:
+        assert max(field_err(o.moments(), m)) < 1e-5
+
+
+@pytest.mark.parametrize("order", [3, 2])
 def test_small_periodic_dimensions(order):
     """Axes shorter than the stencil reach (|v| up to 6 > n): the general modulo path."""
     lat = oracle.read_lattice(order)
@@ -145,7 +170,7 @@ def test_riemann_tube_full_run(order):
     assert max(en, ee, eu) < 1e-12
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("order", [3, 2])
 def test_f32_fields_within_1e5(order, variant):
     """Float storage and arithmetic: Landau fields within 1e-5 of the FP64 oracle after 40 steps of
@@ -202,7 +227,7 @@ def test_autotune_keeps_the_state_and_picks_a_variant():
         a.init(n, T, u)
         b.init(n, T, u)
         v, ms = a.autotune(reps=2)
-        assert 0 <= v <= 3 and all(t > 0 for t in ms)
+        assert 0 <= v < len(ms) and len(ms) == 4 and all(t > 0 for t in ms)
         assert np.array_equal(a.populations(), b.populations())  # autotuning changed nothing
         a.step(1)
         with pytest.raises(RLBError) as e:
@@ -265,8 +290,8 @@ def test_landau_failure_is_reported_not_hidden():
         assert np.array_equal(g.populations()[0], single[0])  # streamed, not collided
 
 
-@pytest.mark.parametrize("storage,tol,variant", [("f64", 1e-12, -1), ("f32", 2e-5, 0), ("f32", 2e-5, 1),
-                                                 ("f32", 2e-5, 2), ("f32", 2e-5, 3)])
+@pytest.mark.parametrize("storage,tol,variant", [("f64", 1e-12, -1)] + [("f32", 2e-5, v) for v in range(6)] +
+                         [("f16dev", 2e-2, v) for v in (0, 3)])
 def test_full_size_sampled_cells(storage, tol, variant):
     """256^3 random-field case in the benchmark's launch configuration: one step from the seeded
     equilibrium, 96 cells (corners, faces, interior, random) against the oracle cell by cell."""

@@ -1,0 +1,53 @@
+"""Serving: continuous batching under an HBM budget; every result equals its solo run."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU containers
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1301_3423_gb300 import RLB  # noqa: E402
+from paper_1301_3423_gb300 import serve  # noqa: E402
+
+
+def solo(req):
+    with RLB(req.shape, order=3, bc=req.bc, eta_over_s=req.eta_over_s, storage=req.storage, landau_fp64=True) as c:
+        c.init(*serve.initial_fields(req))
+        c.step(req.steps)
+        return c.moments()
+
+
+def test_served_results_equal_solo_runs_and_admission_respects_the_budget():
+    reqs = serve.poisson_requests(12, rate=200.0, seed=3, sizes=(16, 24, 32), step_scale=0.02, f16_fraction=0.3)
+    # a budget below the total forces waiting and re-admission
+    sizes = [serve.Server.bytes_of(r) for r in reqs]
+    budget = max(sizes) + 0.3 * (sum(sizes) - max(sizes))
+    srv = serve.Server(hbm_budget=budget, chunk=7)
+    try:
+        st = srv.run(reqs, realtime=False)
+    finally:
+        srv.close()
+    assert st["requests"] == len(reqs)
+    assert srv.peak_in_use <= budget
+    assert srv.peak_active < len(reqs)  # not everything fitted at once
+    by_id = {r.rid: r for r in srv.results}
+    for req in reqs:
+        ref = solo(req)
+        got = by_id[req.rid]
+        assert got.steps == req.steps
+        for key in ("n", "eps", "U", "totals"):
+            assert np.array_equal(getattr(got, key), ref[key]), (req, key)
+
+
+def test_realtime_stream_reports_latency_percentiles():
+    reqs = serve.poisson_requests(10, rate=50.0, seed=9, sizes=(16, 32), step_scale=0.02)
+    srv = serve.Server(hbm_budget=20e9, chunk=10)
+    try:
+        st = srv.run(reqs, realtime=True, max_wall=120)
+    finally:
+        srv.close()
+    assert st["requests"] == 10
+    assert 0 < st["p50_tts_s"] <= st["p99_tts_s"]
+    assert st["aggregate_mlups"] > 0
