@@ -140,11 +140,11 @@ rlb_status rlb_set_populations(rlb_ctx* ctx, const double* f, int on_device);
 #define RLB_MAX_VARIANTS 8
 
 /* Autotuner: time every step-kernel variant of this context on the context's own lattice and keep
- * the fastest for later rlb_step calls.  For float storage the variants differ in arithmetic
- * (scalar, or mirror pairs in paired-FMA float2) and residency (all populations in registers at 2
- * or 3 resident blocks per SM, or part of them staged in shared memory at 4); double storage has
- * one.  Each variant repeats one step from the current populations into the spare buffer `reps`
- * times, so the state does not change; this is allowed only before the first step after rlb_init
+ * the fastest for later rlb_step calls.  For float and half storage variants 0..3 differ in
+ * arithmetic (bit 0: scalar, or mirror pairs in paired-FMA float2) and residency (bit 1: all
+ * populations in registers at 2 or 3 resident blocks per SM).  Double storage has one.  Each
+ * variant repeats one step from the current populations into the spare buffer `reps` times, so the
+ * state does not change; this is allowed only before the first step after rlb_init
  * / rlb_set_populations (RLB_ESTATE otherwise).  *variant (may be NULL) receives the choice;
  * ms[RLB_MAX_VARIANTS] (may be NULL) the milliseconds per step of each variant (0 where a
  * variant does not exist).  Synchronises the stream.
@@ -189,7 +189,8 @@ rlb_status rlb_batch_run(rlb_batch* b, long nsteps, int use_graph, int* active);
  * fastest.  *variant and ms[RLB_MAX_VARIANTS] as for rlb_autotune. */
 rlb_status rlb_batch_autotune(rlb_batch* b, int reps, int* variant, double ms[RLB_MAX_VARIANTS]);
 
-/* Force the batched kernel's step variant (the one rlb_autotune / step_variant number). */
+/* Force the batched kernel's step variant (numbered as for rlb_autotune).
+ * Errors: RLB_EINVAL for a variant the batch's storage does not have. */
 rlb_status rlb_batch_set_variant(rlb_batch* b, int variant);
 
 /* Kernel launches the batch has enqueued (-1 for NULL). */

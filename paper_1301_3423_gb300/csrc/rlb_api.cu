@@ -213,9 +213,10 @@ extern "C" rlb_status rlb_create(const rlb_params* p, rlb_ctx** out) {
   }
   if (in[0] == 0 || in[1] == 0 || in[2] == 0) in[0] = in[1] = in[2] = 0, i0[0] = i0[1] = i0[2] = 0;
   sp.ix0 = i0[0], sp.ixn = in[0], sp.iy0 = i0[1], sp.iyn = in[1], sp.iz0 = i0[2], sp.izn = in[2];
-  sp.int_segs = (in[0] + 31) / 32;
+  // the row kernel takes every row with interior y and z, in 32-aligned x segments; the shell the rest
+  sp.int_segs = in[0] > 0 ? (p->nx + 31) / 32 : 0;
   sp.int_warps = sp.int_segs * in[1] * in[2];
-  sp.shell_cells = c->cells - in[0] * in[1] * in[2];
+  sp.shell_cells = c->cells - (in[0] > 0 ? p->nx * in[1] * in[2] : 0);
 
   const size_t pop_bytes = (size_t)c->q * c->cells * c->elem;
   c->fblocks = (c->cells + kMomThreads - 1) / kMomThreads;

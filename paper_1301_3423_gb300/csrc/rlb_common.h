@@ -25,7 +25,7 @@ struct StepParams {
   int general;              // a periodic axis is shorter than the stencil reach (modulo wrap)
   // Interior box: cells whose whole stencil stays inside the lattice, x in [ix0, ix0 + ixn) etc.
   int ix0, ixn, iy0, iyn, iz0, izn;
-  int int_segs;             // warp-wide segments (32 cells) per interior row
+  int int_segs;             // 32-aligned warp segments per row of the row kernel (all nx cells)
   int int_warps;            // interior segments in total
   int shell_cells;          // cells outside the interior box
 };

@@ -9,7 +9,7 @@ using namespace inst;
 cudaError_t step(const void* src, void* dst, const StepParams& p, int* status, bool general, int variant,
                  cudaStream_t s) {
   if (kFloat) {
-    switch (variant) {
+    switch (variant < kVariants ? variant : 0) {
       case 1: return RLB_VFN(step, 1)(src, dst, p, status, general, s);
       case 2: return RLB_VFN(step, 2)(src, dst, p, status, general, s);
       case 3: return RLB_VFN(step, 3)(src, dst, p, status, general, s);
@@ -22,7 +22,7 @@ cudaError_t step(const void* src, void* dst, const StepParams& p, int* status, b
 cudaError_t batch_step(const BatchMember* m, int n, int tiles, int li, int* counters, int variant, int grid,
                        cudaStream_t s) {
   if (kFloat) {
-    switch (variant) {
+    switch (variant < kVariants ? variant : 0) {
       case 1: return RLB_VFN(batch, 1)(m, n, tiles, li, counters, grid, s);
       case 2: return RLB_VFN(batch, 2)(m, n, tiles, li, counters, grid, s);
       case 3: return RLB_VFN(batch, 3)(m, n, tiles, li, counters, grid, s);
@@ -34,7 +34,7 @@ cudaError_t batch_step(const BatchMember* m, int n, int tiles, int li, int* coun
 
 int batch_blocks_per_sm(int variant) {
   if (kFloat) {
-    switch (variant) {
+    switch (variant < kVariants ? variant : 0) {
       case 1: return RLB_VFN(occupancy, 1)();
       case 2: return RLB_VFN(occupancy, 2)();
       case 3: return RLB_VFN(occupancy, 3)();
@@ -75,7 +75,7 @@ cudaError_t convert_pops(void* pop, double* dbl, int i0, int i1, bool to_f64, co
 #define RLB_CAT_(a, b, c, d) a##b##c##d
 #define RLB_NAME(o, s) RLB_CAT_(launchers_o, o, _s, s)
 extern const Launchers RLB_NAME(RLB_INST_ORDER, RLB_INST_STORAGE) = {
-    step, fields, init, convert_pops, inst::kFloat ? (int)kNumVariants : 1, batch_step, batch_blocks_per_sm};
+    step, fields, init, convert_pops, inst::kVariants, batch_step, batch_blocks_per_sm};
 
 #if RLB_INST_ORDER == 3 && RLB_INST_STORAGE == 0
 // Second pass of the conserved-density sums: one block adds the per-block partials in a fixed

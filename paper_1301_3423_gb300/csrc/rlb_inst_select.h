@@ -32,6 +32,7 @@ using S = StoreF16Dev;
 #endif
 using T = typename S::T;
 constexpr bool kFloat = std::is_same<typename S::A, float>::value;
+constexpr int kVariants = kFloat ? kNumVariants : 1;
 }  // namespace inst
 
 // Per-variant entry points (defined in rlb_inst_variant.cu, one unit per variant).

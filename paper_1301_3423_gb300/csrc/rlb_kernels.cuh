@@ -147,6 +147,14 @@ __device__ __forceinline__ bool is_interior(const Cell& cl, const StepParams& p)
          cl.z >= L::VMAX_Z && cl.z < p.nz - L::VMAX_Z;
 }
 
+// Shift that turns the constant-offset source of population I into its periodic (or clamped)
+// source when only the x coordinate can leave the lattice (rows whose y and z are interior).
+template <class L, int I>
+__device__ __forceinline__ int x_wrap_shift(const Cell& cl, const StepParams& p) {
+  constexpr int vx = L::VX[I];
+  return src_coord<vx, false>(cl.x, p.nx, p.bc[0]) - (cl.x - vx);
+}
+
 // ---------------------------------------------------------------------------------------------
 // moments N^mu, T^{mu nu} (Eqs. (moments:dis1), (moments:dis2)), accumulated over mirror pairs:
 // for a pair (v, -v) at energy p0, s1 = p0 (f+ +- f-), s2 = p0^2 (f+ +- f-).
@@ -533,42 +541,33 @@ __device__ __forceinline__ void collide_f2(const Landau<float>& lw, float T, flo
 //   bit 0: scalar arithmetic (0) or mirror pairs in float2 with paired FMA (1);
 //   bit 1: registers as needed, 2 resident blocks of 128 threads per SM (0), or at most 168
 //          registers for 3 resident blocks (1; the compiler spills a little).
-// (Staging part of the populations in shared memory with cp.async, and pulling every population
-// twice, were measured slower and are not built.)
+// (Staging part of the populations in shared memory, a persistent interior kernel that prefetches
+// each thread's next cell into shared memory with cp.async while it computes the current one, and
+// pulling every population twice were all measured slower and are not built.)
 // Double arithmetic pulls each population twice (moments, then collision) and has one variant.
 enum StepVariant : int {
-  kRegScalar = 0, kRegPacked = 1, kReg3Scalar = 2, kReg3Packed = 3, kSplitScalar = 4, kSplitPacked = 5,
-  kNumVariants = 4
+  kRegScalar = 0, kRegPacked = 1, kReg3Scalar = 2, kReg3Packed = 3, kNumVariants = 4
 };
-
-constexpr int kSplitRegs = 40;
 
 template <class S, int VARIANT>
 struct StepShape {
-  static constexpr int kResidency = VARIANT >> 1;
-  static constexpr bool kSplit = kResidency == 2 && std::is_same<S, StoreF32>::value;
-  static constexpr int kMinBlocks = kResidency == 0 ? 1 : (kSplit ? 4 : 3);
+  static constexpr int kResidency = (VARIANT >> 1) & 1;
+  static constexpr int kMinBlocks = kResidency == 0 ? 1 : 3;
 };
 
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
 
 // How a step kernel pulls: kPathAuto lets each warp vote (all lanes interior: constant offsets,
-// else wrapped / clamped indices); the interior kernel knows every lane is interior; the shell
-// kernel knows none needs to be.
-enum PullPath : int { kPathAuto = 0, kPathInterior = 1, kPathEdge = 2 };
+// else wrapped / clamped indices); the row kernel's warps lie in rows with interior y and z and
+// are told whether their x segment is interior too (else only x wraps); the shell kernel wraps
+// every coordinate.
+enum PullPath : int { kPathAuto = 0, kPathRow = 1, kPathEdge = 2 };
 
 // One cell's time step (pull, moments, Landau matching, equilibrium, collision, store).  Invalid
 // lanes (valid = false) carry a clamped in-range cell, compute and store nothing.
 template <class L, class S, bool GENERAL, int VARIANT, int PATH>
 __device__ __forceinline__ void step_cell(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
                                           const StepParams& p, int* __restrict__ status, const Cell cl,
-                                          const bool valid) {
+                                          const bool valid, const bool row_fast = false) {
   using A = typename S::A;
   using ST = typename S::T;
   constexpr bool PACKED = (VARIANT & 1) && std::is_same<A, float>::value;
@@ -576,7 +575,7 @@ __device__ __forceinline__ void step_cell(const typename S::T* __restrict__ src,
   // Warp-uniform choice: if every lane's stencil stays inside the lattice, pull with constant
   // offsets; otherwise resolve periodic wrap / copy-out per population.
   bool fast;
-  if constexpr (PATH == kPathInterior) fast = true;
+  if constexpr (PATH == kPathRow) fast = row_fast;
   else if constexpr (PATH == kPathEdge) fast = false;
   else fast = __all_sync(0xffffffffu, is_interior<L>(cl, p));
   const ST* __restrict__ base = src + cl.c;
@@ -585,39 +584,23 @@ __device__ __forceinline__ void step_cell(const typename S::T* __restrict__ src,
   auto load = [&](auto I) -> A {
     constexpr int i = decltype(I)::value;
     if (fast) return S::template load<L, i>(base + p.off[i], p);
-    return S::template load<L, i>(src + pull_index<L, i, GENERAL>(cl, p), p);
+    if constexpr (PATH == kPathRow) return S::template load<L, i>(base + (p.off[i] + x_wrap_shift<L, i>(cl, p)), p);
+    else return S::template load<L, i>(src + pull_index<L, i, GENERAL>(cl, p), p);
   };
   auto store = [&](auto I, A v) {
     constexpr int i = decltype(I)::value;
     if (valid) S::template store<L, i>(out + (long long)i * p.cells, v, p);
   };
 
-  constexpr bool SPLIT = StepShape<S, VARIANT>::kSplit;
-  constexpr int KREG = SPLIT ? (L::Q < kSplitRegs ? L::Q : kSplitRegs) : L::Q;
-  constexpr int NSM = SPLIT ? L::Q - KREG : 0;
-  __shared__ float fsm[NSM > 0 ? NSM : 1][kStepThreads];
-  A fk[KEEP ? KREG : 1];
+  A fk[KEEP ? L::Q : 1];
   if constexpr (KEEP) {
-    auto pull_one = [&](auto I, const ST* ptr) {
-      constexpr int i = decltype(I)::value;
-      if constexpr (i < KREG) fk[i] = S::template load<L, i>(ptr, p);
-      else cp_async4(&fsm[i - KREG][threadIdx.x], ptr);
-    };
-    if (fast) {
-      static_for<L::Q>([&](auto I) { pull_one(I, base + p.off[decltype(I)::value]); });
-    } else {
-      static_for<L::Q>([&](auto I) { pull_one(I, src + pull_index<L, decltype(I)::value, GENERAL>(cl, p)); });
-    }
-    if constexpr (NSM > 0) cp_async_wait_all();  // each thread reads only its own slots
+    // one warp-uniform branch around the whole pull, so the fast path is plain constant offsets
+    if (fast) static_for<L::Q>([&](auto I) { fk[decltype(I)::value] = S::template load<L, decltype(I)::value>(base + p.off[decltype(I)::value], p); });
+    else static_for<L::Q>([&](auto I) { fk[decltype(I)::value] = load(I); });
   }
   auto get = [&](auto I) -> A {
-    constexpr int i = decltype(I)::value;
-    if constexpr (KEEP) {
-      if constexpr (i < KREG) return fk[i];
-      else return (A)fsm[i - KREG][threadIdx.x];
-    } else {
-      return load(I);
-    }
+    if constexpr (KEEP) return fk[decltype(I)::value];
+    else return load(I);
   };
   auto get2 = [&](auto I) -> float2 {
     constexpr int i = decltype(I)::value;
@@ -651,27 +634,36 @@ __device__ __forceinline__ void step_cell(const typename S::T* __restrict__ src,
 }
 
 
-// Interior cells: warp w covers 32 consecutive x of one interior row (the last segment of a row
-// may be partial); every lane pulls with constant offsets.
+// Cell of lane `lane` in row-kernel warp w (see k_step_interior).
+__device__ __forceinline__ void row_cell(int w, int lane, const StepParams& p, Cell& cl, bool& valid, bool& fast) {
+  const int seg = w % p.int_segs, row = w / p.int_segs;
+  cl.y = p.iy0 + row % p.iyn;
+  cl.z = p.iz0 + row / p.iyn;
+  const int x0 = seg * 32, x = x0 + lane;
+  valid = x < p.nx;
+  cl.x = valid ? x : p.nx - 1;
+  cl.c = (cl.z * p.ny + cl.y) * p.nx + cl.x;
+  fast = x0 >= p.ix0 && min(x0 + 31, p.nx - 1) < p.ix0 + p.ixn;
+}
+
+// Interior rows (y and z inside the interior box, every x): warp w covers the 32-aligned x segment
+// w % int_segs of row w / int_segs (the last segment may be partial).  A segment inside the
+// interior x range pulls with constant offsets; the others wrap only x.  Whole rows in one kernel
+// keep every sector of a row written by neighbouring warps.
 template <class L, class S, int VARIANT>
 __global__ void __launch_bounds__(kStepThreads, StepShape<S, VARIANT>::kMinBlocks)
     k_step_interior(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
                     const __grid_constant__ StepParams p, int* __restrict__ status) {
   const int w = blockIdx.x * (kStepThreads / 32) + (threadIdx.x >> 5);
   if (w >= p.int_warps) return;  // whole warps only
-  const int seg = w % p.int_segs, row = w / p.int_segs;
   Cell cl;
-  cl.y = p.iy0 + row % p.iyn;
-  cl.z = p.iz0 + row / p.iyn;
-  const int xr = seg * 32 + (threadIdx.x & 31);
-  const bool valid = xr < p.ixn;
-  cl.x = p.ix0 + (valid ? xr : p.ixn - 1);
-  cl.c = (cl.z * p.ny + cl.y) * p.nx + cl.x;
-  step_cell<L, S, false, VARIANT, kPathInterior>(src, dst, p, status, cl, valid);
+  bool valid, fast;
+  row_cell(w, threadIdx.x & 31, p, cl, valid, fast);
+  step_cell<L, S, false, VARIANT, kPathRow>(src, dst, p, status, cl, valid, fast);
 }
 
-// Shell cells (outside the interior box): z-boundary planes, then y-boundary rows of the interior
-// planes, then x-boundary cells of the interior rows; wrapped / clamped pulls.
+// Shell cells (rows whose y or z lies outside the interior box): z-boundary planes, then the
+// y-boundary rows of the interior planes; wrapped / clamped pulls.
 __device__ __forceinline__ Cell shell_cell(int s, const StepParams& p) {
   Cell cl;
   const int A = (p.nz - p.izn) * p.nxy;
@@ -683,23 +675,11 @@ __device__ __forceinline__ Cell shell_cell(int s, const StepParams& p) {
   } else {
     s -= A;
     const int rowy = (p.ny - p.iyn) * p.nx;
-    const int B = rowy * p.izn;
-    if (s < B) {
-      const int zz = s / rowy, r = s - zz * rowy;
-      cl.z = p.iz0 + zz;
-      const int yy = r / p.nx;
-      cl.y = yy < p.iy0 ? yy : yy + p.iyn;
-      cl.x = r - yy * p.nx;
-    } else {
-      s -= B;
-      const int wx = p.nx - p.ixn;
-      const int per_z = wx * p.iyn;
-      const int zz = s / per_z, r = s - zz * per_z;
-      cl.z = p.iz0 + zz;
-      const int yy = r / wx, xx = r - yy * wx;
-      cl.y = p.iy0 + yy;
-      cl.x = xx < p.ix0 ? xx : xx + p.ixn;
-    }
+    const int zz = s / rowy, r = s - zz * rowy;
+    cl.z = p.iz0 + zz;
+    const int yy = r / p.nx;
+    cl.y = yy < p.iy0 ? yy : yy + p.iyn;
+    cl.x = r - yy * p.nx;
   }
   cl.c = (cl.z * p.ny + cl.y) * p.nx + cl.x;
   return cl;
