@@ -184,6 +184,10 @@ extern "C" rlb_status rlb_create(const rlb_params* p, rlb_ctx** out) {
   sp.tau_coef = (p->tau_prime > 0.5) ? 0.0 : 6.0 * p->eta_over_s / (R * kappa);
   sp.tau_local = p->tau_local_T ? 1 : 0;
   sp.T_ref = p->T_ref;
+  sp.tau_is_fixed = sp.tau_fixed > 0.5 ? 1 : 0;
+  sp.tau_fixed_f = (float)sp.tau_fixed;
+  sp.tau_coef_f = (float)sp.tau_coef;
+  sp.T_ref_f = (float)sp.T_ref;
   sp.gamma_thr2 = (float)(p->gamma_thr * p->gamma_thr);
   sp.landau_fp64 = p->landau_fp64 ? 1 : 0;
   sp.half_nref = (float)(0.5 * p->n_ref);

@@ -19,6 +19,9 @@ struct StepParams {
   double tau_coef;          // tau' = 1/2 + tau_coef / T
   int tau_local;            // T = local Landau temperature (1) or T_ref (0)
   double T_ref;
+  // the same in float for the float step paths (no double instruction on their hot path)
+  int tau_is_fixed;
+  float tau_fixed_f, tau_coef_f, T_ref_f;
   float gamma_thr2;         // reduced-precision paths: Landau in double above this gamma^2
   int landau_fp64;
   float half_nref;          // F16DEV: n_ref / 2

@@ -302,9 +302,15 @@ __device__ __forceinline__ Landau<A> landau_step(const Mom<A>& m, const StepPara
 
 template <class A>
 __device__ __forceinline__ A tau_prime(A T, const StepParams& p) {
-  if (p.tau_fixed > 0.5) return A(p.tau_fixed);
-  const A Tt = p.tau_local ? T : A(p.T_ref);
-  return A(0.5) + A(p.tau_coef) / Tt;
+  if constexpr (std::is_same<A, double>::value) {
+    if (p.tau_is_fixed) return p.tau_fixed;
+    const double Tt = p.tau_local ? T : p.T_ref;
+    return 0.5 + p.tau_coef / Tt;
+  } else {
+    if (p.tau_is_fixed) return p.tau_fixed_f;
+    const float Tt = p.tau_local ? T : p.T_ref_f;
+    return 0.5f + p.tau_coef_f / Tt;
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -541,20 +547,20 @@ __device__ __forceinline__ void collide_f2(const Landau<float>& lw, float T, flo
 //   bit 0: scalar arithmetic (0) or mirror pairs in float2 with paired FMA (1);
 //   bit 1: registers as needed, 2 resident blocks of 128 threads per SM (0), or at most 168
 //          registers for 3 resident blocks (1; the compiler spills a little).
-// (Staging part of the populations in shared memory, a persistent interior kernel that prefetches
-// each thread's next cell into shared memory with cp.async while it computes the current one, and
-// pulling every population twice were all measured slower and are not built.)
+// (Also measured slower and not built: staging part of the populations in shared memory; a
+// persistent interior kernel that prefetches each thread's next cell into shared memory with
+// cp.async while it computes the current one; and two passes over the populations, moments then
+// collision, at 64-80 registers and 6-8 resident blocks with L2 evict-last / evict-first hints,
+// whose second pass executed about 50% more instructions and still missed L2 on a third of its
+// reads.)
 // Double arithmetic pulls each population twice (moments, then collision) and has one variant.
-enum StepVariant : int {
-  kRegScalar = 0, kRegPacked = 1, kReg3Scalar = 2, kReg3Packed = 3, kNumVariants = 4
-};
+enum StepVariant : int { kRegScalar = 0, kRegPacked = 1, kReg3Scalar = 2, kReg3Packed = 3, kNumVariants = 4 };
 
 template <class S, int VARIANT>
 struct StepShape {
-  static constexpr int kResidency = (VARIANT >> 1) & 1;
-  static constexpr int kMinBlocks = kResidency == 0 ? 1 : 3;
+  static constexpr bool kKeep = std::is_same<typename S::A, float>::value;  // populations in registers
+  static constexpr int kMinBlocks = (VARIANT & 2) ? 3 : 1;
 };
-
 
 // How a step kernel pulls: kPathAuto lets each warp vote (all lanes interior: constant offsets,
 // else wrapped / clamped indices); the row kernel's warps lie in rows with interior y and z and
@@ -571,7 +577,7 @@ __device__ __forceinline__ void step_cell(const typename S::T* __restrict__ src,
   using A = typename S::A;
   using ST = typename S::T;
   constexpr bool PACKED = (VARIANT & 1) && std::is_same<A, float>::value;
-  constexpr bool KEEP = std::is_same<A, float>::value;
+  constexpr bool KEEP = StepShape<S, VARIANT>::kKeep;
   // Warp-uniform choice: if every lane's stencil stays inside the lattice, pull with constant
   // offsets; otherwise resolve periodic wrap / copy-out per population.
   bool fast;

@@ -42,7 +42,7 @@ def make(order, storage, variant, k, stream=None):
 
 
 @pytest.mark.parametrize("order,storage,variant", [(3, "f32", 0), (3, "f32", 3), (3, "f64", -1), (2, "f32", 1),
-                                                   (3, "f16dev", 0)])
+                                                   (3, "f16dev", 0), (3, "f16dev", 3)])
 @pytest.mark.parametrize("graph", [True, False])
 def test_batched_members_equal_solo_runs(order, storage, variant, graph):
     solo = []
