@@ -19,6 +19,7 @@ Multi-GPU (torchrun): every rank steps its own independent lattice (replicas; no
 data path); value = all ranks' cell updates / the slowest rank's time.
 """
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -109,6 +110,33 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+# Sources that decide the step kernels' memory traffic: a DRAM-traffic record taken with ncu is
+# used only while these are byte-for-byte the ones it was taken on.
+TRAFFIC_SOURCES = ("rlb_kernels.cuh", "rlb_common.h", "rlb_inst_variant.cu")
+
+
+def kernel_sources_digest():
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_1301_3423_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(n_side, variant, density):
+    """DRAM bytes (read + write) of one step from profiles/step_f32_traffic.json, or None when the
+    record is missing or was taken on other kernel sources, another variant or lattice."""
+    path = os.path.join(ROOT, "profiles", "step_f32_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if (rec.get("sources_sha256") != kernel_sources_digest() or rec.get("variant") != variant
+            or rec.get("lattice") != n_side or rec.get("density") != density):
+        return None
+    return rec.get("dram_bytes_per_step")
 
 
 def dist_setup():
@@ -353,13 +381,7 @@ def main():
     algo_bytes = cells * Q * 2 * 4
     peaks, peak_src = measured_peaks()
     achieved = algo_bytes / per_step_s / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "step_f32_traffic.json")
-    if os.path.exists(tpath):
-        try:
-            traffic = json.load(open(tpath)).get("bytes_per_launch_256")
-        except (OSError, ValueError):
-            traffic = None
+    traffic = recorded_traffic(N, variant, args.density)
     g.close()
 
     # ---- FP64 plain path on the same lattice ------------------------------------------------
