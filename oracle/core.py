@@ -171,6 +171,7 @@ class OracleRLB:
 
     def __init__(self, lat, nx, ny, nz, bc=(0, 0, 0), eta_over_s=0.1, tau_prime=0.0, tau_local_T=1, T_ref=1.0,
                  dx_fm=0.008, T_unit_GeV=0.4):
+        """bc per axis (x, y, z): 0 periodic, 1 copy-out, 2 bounce-back wall."""
         self.lat = lat
         self.shape = (nz, ny, nx)
         self.nx, self.ny, self.nz = nx, ny, nz
@@ -200,11 +201,14 @@ class OracleRLB:
 
     def _call(self, fin, fout, pull, collide, fields=None, dens=None):
         lat = self.lat
-        return _load().ora_step(lat.order, lat.q, _ip(lat.v), _dp(lat.p0), _dp(lat.w), _dp(lat.gs), self.nx,
-                                self.ny, self.nz,
-                                _ip(self.bc), self.eta_over_s, self.tau_prime, self.tau_local_T, self.T_ref,
-                                self.dx_fm, self.T_unit_GeV, pull, collide, _dp(fin), _dp(fout), _dp(fields),
-                                _dp(dens))
+        bad = _load().ora_step(lat.order, lat.q, _ip(lat.v), _dp(lat.p0), _dp(lat.w), _dp(lat.gs), self.nx,
+                               self.ny, self.nz,
+                               _ip(self.bc), self.eta_over_s, self.tau_prime, self.tau_local_T, self.T_ref,
+                               self.dx_fm, self.T_unit_GeV, pull, collide, _dp(fin), _dp(fout), _dp(fields),
+                               _dp(dens))
+        if bad < 0:
+            raise ValueError("bounce-back walls need a reversed partner for every population")
+        return bad
 
     def step(self, k=1):
         for _ in range(k):

@@ -21,6 +21,14 @@
  *   - Anderson-Witting BGK collision f_i <- f_i - (p_i^mu U_mu)/(tau' p_i^0) (f_i - f_i^eq)
  *     (Eq. (rlb:disc), right-hand side, with delta t' = 1).
  *
+ * Boundaries, per axis: periodic, copy-out (a pull source beyond the end is the nearest edge cell)
+ * or bounce-back wall.  The paper asks for weights equal under p -> -p (spatial part) so that the
+ * classical bounce-back rule conserves mass and energy at solid walls (Sec. II.C); it states no
+ * rule for links longer than one cell.  Here a population whose pull source lies beyond a
+ * bounce-back wall is replaced by the same cell's post-collision population of the reversed
+ * momentum (same p0, -v), i.e. every population that would leave through the wall comes back
+ * reversed into the cell it left.
+ *
  * Conventions: lattice units delta x = delta t' = 1, metric diag(+,-,-,-),
  * p_i^mu = p0_i (1, v_i / R) (Eq. (eq:mrecon2)).  Populations are stored f[i][z][y][x].
  * The stored state is post-collision; a step is pull, then collide.
@@ -251,6 +259,8 @@ double ora_tau_prime(double eta_over_s, double R, double kappa, double T) {
   return 0.5 + 6.0 * eta_over_s / (R * kappa * T);
 }
 
+/* Source coordinate of a pull along one axis (bc 0 periodic, 1 copy-out; a bounce-back axis, 2,
+ * never gets here with s outside [0, n): see beyond_wall). */
 static inline long wrap_index(long s, long n, int bc) {
   if (bc == 0) { /* periodic */
     s %= n;
@@ -260,6 +270,23 @@ static inline long wrap_index(long s, long n, int bc) {
   if (s < 0) return 0; /* copy-out: nearest edge cell */
   if (s >= n) return n - 1;
   return s;
+}
+
+/* 1 if the pull source (x, y, z) - v_i lies beyond a bounce-back wall. */
+static inline int beyond_wall(const int* bc, long x, long y, long z, int nx, int ny, int nz, const int* vi) {
+  const long s[3] = {x - vi[0], y - vi[1], z - vi[2]};
+  const long n[3] = {nx, ny, nz};
+  for (int a = 0; a < 3; ++a)
+    if (bc[a] == 2 && (s[a] < 0 || s[a] >= n[a])) return 1;
+  return 0;
+}
+
+/* Index of the population with the reversed momentum (same p0, -v) of population i. */
+static int reversed_population(int q, const int* v, const double* p0, int i) {
+  for (int j = 0; j < q; ++j)
+    if (v[3 * j] == -v[3 * i] && v[3 * j + 1] == -v[3 * i + 1] && v[3 * j + 2] == -v[3 * i + 2] && p0[j] == p0[i])
+      return j;
+  return -1;
 }
 
 /* Moments, Landau matching, relaxation time, equilibrium and collision of one cell whose pulled
@@ -307,8 +334,9 @@ static int collide_cell(int order, int q, const int* v, const double* p0, const 
  * If dens != NULL it receives the conserved densities N^0, T^00, T^0x, T^0y, T^0z per cell.
  * collide = 0 only pulls and evaluates (fields / dens); pull = 0 reads each cell in place.
  * tau_prime > 0.5 fixes tau'; otherwise tau' follows eta/s with the local (tau_local_T = 1) or the
- * reference temperature.  Returns the number of cells where Landau matching failed (those cells
- * are copied without collision and get NaN fields).
+ * reference temperature.  bc[a] per axis: 0 periodic, 1 copy-out, 2 bounce-back wall.  Returns the
+ * number of cells where Landau matching failed (those cells are copied without collision and get
+ * NaN fields), or -1 if a bounce-back wall is asked for and a population has no reversed partner.
  */
 long ora_step(int order, int q, const int* v, const double* p0, const double* w, const double* gs, int nx, int ny,
               int nz,
@@ -319,11 +347,20 @@ long ora_step(int order, int q, const int* v, const double* p0, const double* w,
   const size_t cells = (size_t)nx * ny * nz;
   long bad = 0;
   double ft[ORA_QMAX], fo[ORA_QMAX], fld[6], dn[5];
+  int rev[ORA_QMAX];
+  for (int i = 0; i < q; ++i) {
+    rev[i] = reversed_population(q, v, p0, i);
+    if (rev[i] < 0 && (bc[0] == 2 || bc[1] == 2 || bc[2] == 2)) return -1;
+  }
   for (long z = 0; z < nz; ++z)
     for (long y = 0; y < ny; ++y)
       for (long x = 0; x < nx; ++x) {
         const size_t c = ((size_t)z * ny + y) * nx + x;
         for (int i = 0; i < q; ++i) {
+          if (pull && beyond_wall(bc, x, y, z, nx, ny, nz, v + 3 * i)) {
+            ft[i] = fin[(size_t)rev[i] * cells + c]; /* bounced back at the wall */
+            continue;
+          }
           long sx = x, sy = y, sz = z;
           if (pull) {
             sx = wrap_index(x - v[3 * i + 0], nx, bc[0]);
@@ -366,17 +403,26 @@ long ora_init_step_cells(int order, int q, const int* v, const double* p0, const
     const long c = sample[k];
     const long x = c % nx, y = (c / nx) % ny, z = c / ((long)nx * ny);
     for (int i = 0; i < q; ++i) {
-      const long sx = wrap_index(x - v[3 * i + 0], nx, bc[0]);
-      const long sy = wrap_index(y - v[3 * i + 1], ny, bc[1]);
-      const long sz = wrap_index(z - v[3 * i + 2], nz, bc[2]);
-      const size_t s = ((size_t)sz * ny + sy) * nx + sx;
+      /* source cell and source population (the reversed one, in place, beyond a wall) */
+      int src_i = i;
+      size_t s;
+      if (beyond_wall(bc, x, y, z, nx, ny, nz, v + 3 * i)) {
+        src_i = reversed_population(q, v, p0, i);
+        if (src_i < 0) return -1;
+        s = (size_t)c;
+      } else {
+        const long sx = wrap_index(x - v[3 * i + 0], nx, bc[0]);
+        const long sy = wrap_index(y - v[3 * i + 1], ny, bc[1]);
+        const long sz = wrap_index(z - v[3 * i + 2], nz, bc[2]);
+        s = ((size_t)sz * ny + sy) * nx + sx;
+      }
       const double ux = u[s], uy = u[cells + s], uz = u[2 * cells + s];
       const double u2 = ux * ux + uy * uy + uz * uz;
       if (!(u2 < 1.0) || !(T[s] > 0.0) || !(n[s] > 0.0)) return -1;
       const double g = 1.0 / sqrt(1.0 - u2);
       const double U[4] = {g, g * ux, g * uy, g * uz};
-      /* population i of the source cell: its equilibrium, evaluated for that population only */
-      ora_equilibrium_cell(order, 1, w + i, gs + (size_t)i * nm, n[s], T[s], U, feq);
+      /* population src_i of the source cell: its equilibrium, evaluated for that population only */
+      ora_equilibrium_cell(order, 1, w + src_i, gs + (size_t)src_i * nm, n[s], T[s], U, feq);
       ft[i] = feq[0];
     }
     if (collide_cell(order, q, v, p0, w, gs, eta_over_s, tau_prime, tau_local_T, T_ref, kappa, 1, ft, out + k * q,

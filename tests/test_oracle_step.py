@@ -24,20 +24,35 @@ def near_equilibrium(lat, shape, seed, amp=0.02, vmax=0.3):
     return o.f + amp * scale * rng.standard_normal(o.f.shape)
 
 
+def reversed_index(lat):
+    """rev[i]: the population with the same p0 and velocity -v_i."""
+    key = {(tuple(v), p) for v, p in zip(lat.v.tolist(), lat.p0.tolist())}
+    assert len(key) == lat.q
+    where = {(tuple(v), p): i for i, (v, p) in enumerate(zip(lat.v.tolist(), lat.p0.tolist()))}
+    return np.array([where[(tuple(-np.array(v)), p)] for v, p in zip(lat.v.tolist(), lat.p0.tolist())])
+
+
 def pull(lat, f, bc):
+    """Pull streaming per axis: 0 periodic, 1 copy-out (clamp), 2 bounce-back wall (a source beyond
+    the wall is replaced by the same cell's population of the reversed momentum)."""
     nz, ny, nx = f.shape[1:]
     out = np.empty_like(f)
+    rev = reversed_index(lat)
     for i, (vx, vy, vz) in enumerate(lat.v):
-        idx = []
+        idx, beyond = [], np.zeros((nz, ny, nx), dtype=bool)
         for ax, (nn, vv) in enumerate(((nz, vz), (ny, vy), (nx, vx))):
             src = np.arange(nn) - vv
             b = bc[2 - ax]
             idx.append(np.mod(src, nn) if b == 0 else np.clip(src, 0, nn - 1))
-        out[i] = f[i][np.ix_(*idx)]
+            if b == 2:
+                shape = [1, 1, 1]
+                shape[ax] = nn
+                beyond |= ((src < 0) | (src >= nn)).reshape(shape)
+        out[i] = np.where(beyond, f[rev[i]], f[i][np.ix_(*idx)])
     return out
 
 
-@pytest.mark.parametrize("bc", [(0, 0, 0), (0, 1, 1)])
+@pytest.mark.parametrize("bc", [(0, 0, 0), (0, 1, 1), (2, 0, 2), (2, 2, 2)])
 def test_streaming_moves_population_i_by_v_i(lat3, bc):
     """Eq. (rlb:disc) left-hand side: f_i(x + v_i, t + 1) is built from f_i(x, t).  With a relaxation
     time of 1e15 the collision changes nothing above 1e-15, so one step is a pure shift."""
@@ -83,6 +98,59 @@ def test_conservation_periodic(order):
     assert np.max(np.abs(t1 - t0)) < 1e-13 * np.max(np.abs(t0))
 
 
+@pytest.mark.parametrize("order", [3, 2])
+def test_rest_state_between_walls_is_stationary(order):
+    """Sec. II.C: with weights equal under v -> -v, a bounced population w_i E(p0) comes back as
+    w_{-i} E(p0) = w_i E(p0), so the rest equilibrium in a closed box is a fixed point."""
+    lat = oracle.read_lattice(order)
+    o = oracle.OracleRLB(lat, 5, 4, 7, bc=(2, 2, 2), eta_over_s=0.1)
+    o.init(0.9, 1.1, np.zeros((3, 1, 1, 1)))
+    f0 = o.f.copy()
+    o.step(100)
+    scale = lat.w[:, None, None, None] * 0.9 / 2
+    assert np.max(np.abs(o.f - f0) / scale) < 100 * 1e-13
+
+
+@pytest.mark.parametrize("order", [3, 2])
+def test_walls_conserve_mass_and_energy(order):
+    """Bounce-back returns every population that would cross a wall, with its p0, to the cell it
+    left: sum N^0 and sum T^00 stay invariant in a closed box and in a channel.  The reversal also
+    flips the tangential velocity (a no-slip wall), so no momentum component is conserved."""
+    lat = oracle.read_lattice(order)
+    shape = (6, 4, 5)
+    f = near_equilibrium(lat, shape, seed=12, amp=0.05, vmax=0.5)
+    for bc in ((2, 2, 2), (0, 0, 2)):
+        o = oracle.OracleRLB(lat, shape[2], shape[1], shape[0], bc=bc, eta_over_s=0.1)
+        o.set_populations(f)
+        t0 = o.moments()[3]
+        o.step(25)
+        t1 = o.moments()[3]
+        assert o.nonconv == 0
+        tol = 1e-13 * np.max(np.abs(t0))
+        assert abs(t1[0] - t0[0]) < tol and abs(t1[1] - t0[1]) < tol
+        assert np.min(np.abs(t1[2:] - t0[2:])) > 1e3 * tol  # the walls take up momentum
+
+
+@pytest.mark.parametrize("order", [3, 2])
+def test_no_slip_walls_brake_a_tangential_flow(order):
+    """A uniform flow along x in a 48-cell channel between bounce-back walls normal to z loses its x
+    momentum to the walls (to below 2 % within 80 steps), while the periodic lattice without walls
+    keeps it exactly."""
+    lat = oracle.read_lattice(order)
+    px = {}
+    for bc in ((0, 0, 2), (0, 0, 0)):
+        o = oracle.OracleRLB(lat, 1, 1, 48, bc=bc, eta_over_s=0.1)
+        o.init(1.0, 1.0, np.array([0.1, 0.0, 0.0])[:, None, None, None])
+        series = [o.moments()[3][2]]
+        for _ in range(8):
+            o.step(10)
+            series.append(o.moments()[3][2])
+        px[bc] = np.array(series)
+    wall = px[(0, 0, 2)]
+    assert wall[1] < wall[0] and wall[2] < wall[1] and abs(wall[-1]) < 0.02 * wall[0]
+    assert np.max(np.abs(px[(0, 0, 0)] - px[(0, 0, 0)][0])) < 1e-13 * px[(0, 0, 0)][0]
+
+
 def numpy_step(lat, f, bc, tau):
     """One step written independently with numpy: np indexing for the pull, einsum moments, a dense
     eigen-solver for Landau matching, the Gram-Schmidt projection for f^eq."""
@@ -109,7 +177,7 @@ def numpy_step(lat, f, bc, tau):
 
 
 @pytest.mark.parametrize("order", [3, 2])
-@pytest.mark.parametrize("bc", [(0, 0, 0), (1, 0, 1)])
+@pytest.mark.parametrize("bc", [(0, 0, 0), (1, 0, 1), (0, 2, 2)])
 def test_step_matches_independent_numpy_step(order, bc):
     lat = oracle.read_lattice(order)
     shape = (3, 2, 4)
