@@ -50,7 +50,16 @@ typedef enum {
   RLB_ESTATE = 7    /* call not valid in the context's current state */
 } rlb_status;
 
-typedef enum { RLB_BC_PERIODIC = 0, RLB_BC_COPYOUT = 1 } rlb_bc;
+/* Boundary condition of one axis, applied at both ends.
+ *   RLB_BC_PERIODIC  : the pull wraps around.
+ *   RLB_BC_COPYOUT   : a population pulled from beyond an end is taken from the nearest edge cell.
+ *   RLB_BC_BOUNCEBACK: solid walls just beyond both ends.  A population whose pull source lies
+ *                      beyond a wall is the same cell's post-collision population of the reversed
+ *                      momentum (same p0, -v): everything that would cross the wall comes back
+ *                      reversed into the cell it left, so sum N^0 and sum T^00 are conserved and
+ *                      the wall is no-slip.  The weights are equal under v -> -v for this purpose
+ *                      (Sec. II.C); the paper states no rule for links longer than one cell. */
+typedef enum { RLB_BC_PERIODIC = 0, RLB_BC_COPYOUT = 1, RLB_BC_BOUNCEBACK = 2 } rlb_bc;
 
 /* Storage precision of the populations in device memory.
  *   RLB_F64   : double populations, double arithmetic.
@@ -63,8 +72,7 @@ typedef struct {
   int order;          /* 3: third-order model, R^2 = 41, Q = 128 (Sec. II.C); 2: second order,
                          R^2 = 9, Q = 66 (App. A) */
   int nx, ny, nz;     /* lattice size in cells, each >= 1 */
-  int bc[3];          /* per axis x, y, z: RLB_BC_PERIODIC, or RLB_BC_COPYOUT (a population pulled
-                         from outside the lattice is taken from the nearest edge cell) */
+  int bc[3];          /* per axis x, y, z: an rlb_bc value (periodic, copy-out or bounce-back) */
   double eta_over_s;  /* shear viscosity over entropy density; mapped to tau' by
                          tau' = 1/2 + 6 (eta/s) / (R kappa T), kappa = T_unit_GeV dx_fm / (hbar c)
                          (Sec. II.D, Sec. III), unless tau_prime > 1/2 */

@@ -103,7 +103,8 @@ static std::string validate(const rlb_params* p) {
   const long long cells = (long long)p->nx * p->ny * p->nz;
   if (cells > 0x7fffffffll) return "more than 2^31 - 1 cells";
   for (int a = 0; a < 3; ++a)
-    if (p->bc[a] != RLB_BC_PERIODIC && p->bc[a] != RLB_BC_COPYOUT) return "bc must be periodic or copy-out";
+    if (p->bc[a] != RLB_BC_PERIODIC && p->bc[a] != RLB_BC_COPYOUT && p->bc[a] != RLB_BC_BOUNCEBACK)
+      return "bc must be periodic, copy-out or bounce-back";
   if (p->storage != RLB_F64 && p->storage != RLB_F32 && p->storage != RLB_F16DEV) return "unknown storage";
   if (!(p->tau_prime > 0.5)) {
     if (!(p->eta_over_s > 0) || !std::isfinite(p->eta_over_s)) return "eta_over_s must be > 0 (or tau_prime > 1/2)";
@@ -149,6 +150,8 @@ static void fill_offsets(StepParams& sp) {
 
 template <class L>
 static bool needs_general_wrap(const rlb_params& p) {
+  static_assert(RLB_BC_PERIODIC == kPeriodic && RLB_BC_COPYOUT == kCopyOut && RLB_BC_BOUNCEBACK == kBounceBack,
+                "boundary codes of the ABI and the kernels agree");
   return (p.bc[0] == RLB_BC_PERIODIC && p.nx < L::VMAX_X) || (p.bc[1] == RLB_BC_PERIODIC && p.ny < L::VMAX_Y) ||
          (p.bc[2] == RLB_BC_PERIODIC && p.nz < L::VMAX_Z);
 }
@@ -178,6 +181,7 @@ extern "C" rlb_status rlb_create(const rlb_params* p, rlb_ctx** out) {
   sp.nxy = p->nx * p->ny;
   sp.cells = c->cells;
   for (int a = 0; a < 3; ++a) sp.bc[a] = p->bc[a];
+  sp.has_wall = (p->bc[0] == RLB_BC_BOUNCEBACK || p->bc[1] == RLB_BC_BOUNCEBACK || p->bc[2] == RLB_BC_BOUNCEBACK);
   const double R = p->order == 3 ? Quad3::R : Quad2::R;
   sp.tau_fixed = p->tau_prime > 0.5 ? p->tau_prime : 0.0;
   const double kappa = p->T_unit_GeV * p->dx_fm / kHbarcGeVfm;

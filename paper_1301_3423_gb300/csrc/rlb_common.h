@@ -26,12 +26,16 @@ struct StepParams {
   int landau_fp64;
   float half_nref;          // F16DEV: n_ref / 2
   int general;              // a periodic axis is shorter than the stencil reach (modulo wrap)
+  int has_wall;             // some axis has bounce-back walls (bc == kBounceBack)
   // Interior box: cells whose whole stencil stays inside the lattice, x in [ix0, ix0 + ixn) etc.
   int ix0, ixn, iy0, iyn, iz0, izn;
   int int_segs;             // 32-aligned warp segments per row of the row kernel (all nx cells)
   int int_warps;            // interior segments in total
   int shell_cells;          // cells outside the interior box
 };
+
+// per-axis boundary codes, as in rlb_bc
+enum : int { kPeriodic = 0, kCopyOut = 1, kBounceBack = 2 };
 
 enum : int { kStatusNonconv = 0, kStatusBadInit = 1, kStatusWords = 4 };
 

@@ -132,9 +132,22 @@ __device__ __forceinline__ int src_coord(int x, int n, int bc) {
   }
 }
 
+// True if the pull source of population I lies beyond a bounce-back wall (then the cell takes its
+// own population of the reversed momentum, I ^ 1: mirror pairs are adjacent).
+template <class L, int I>
+__device__ __forceinline__ bool beyond_wall(const Cell& cl, const StepParams& p) {
+  constexpr int vx = L::VX[I], vy = L::VY[I], vz = L::VZ[I];
+  bool b = false;
+  if constexpr (vx != 0) b = b || (p.bc[0] == kBounceBack && (unsigned)(cl.x - vx) >= (unsigned)p.nx);
+  if constexpr (vy != 0) b = b || (p.bc[1] == kBounceBack && (unsigned)(cl.y - vy) >= (unsigned)p.ny);
+  if constexpr (vz != 0) b = b || (p.bc[2] == kBounceBack && (unsigned)(cl.z - vz) >= (unsigned)p.nz);
+  return b;
+}
+
 template <class L, int I, bool GENERAL>
 __device__ __forceinline__ long long pull_index(const Cell& cl, const StepParams& p) {
   constexpr int vx = L::VX[I], vy = L::VY[I], vz = L::VZ[I];
+  if (p.has_wall && beyond_wall<L, I>(cl, p)) return (long long)(I ^ 1) * p.cells + cl.c;
   const int sx = src_coord<vx, GENERAL>(cl.x, p.nx, p.bc[0]);
   const int sy = src_coord<vy, GENERAL>(cl.y, p.ny, p.bc[1]);
   const int sz = src_coord<vz, GENERAL>(cl.z, p.nz, p.bc[2]);
@@ -147,12 +160,16 @@ __device__ __forceinline__ bool is_interior(const Cell& cl, const StepParams& p)
          cl.z >= L::VMAX_Z && cl.z < p.nz - L::VMAX_Z;
 }
 
-// Shift that turns the constant-offset source of population I into its periodic (or clamped)
-// source when only the x coordinate can leave the lattice (rows whose y and z are interior).
+// Pull offset of population I from the cell's own index when only the x coordinate can leave the
+// lattice (rows whose y and z are interior): the constant offset with x wrapped or clamped, or the
+// cell's own reversed population beyond a bounce-back wall in x.
 template <class L, int I>
-__device__ __forceinline__ int x_wrap_shift(const Cell& cl, const StepParams& p) {
+__device__ __forceinline__ long long x_row_offset(const Cell& cl, const StepParams& p) {
   constexpr int vx = L::VX[I];
-  return src_coord<vx, false>(cl.x, p.nx, p.bc[0]) - (cl.x - vx);
+  if constexpr (vx != 0) {
+    if (p.bc[0] == kBounceBack && (unsigned)(cl.x - vx) >= (unsigned)p.nx) return (long long)(I ^ 1) * p.cells;
+  }
+  return p.off[I] + (src_coord<vx, false>(cl.x, p.nx, p.bc[0]) - (cl.x - vx));
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -590,7 +607,7 @@ __device__ __forceinline__ void step_cell(const typename S::T* __restrict__ src,
   auto load = [&](auto I) -> A {
     constexpr int i = decltype(I)::value;
     if (fast) return S::template load<L, i>(base + p.off[i], p);
-    if constexpr (PATH == kPathRow) return S::template load<L, i>(base + (p.off[i] + x_wrap_shift<L, i>(cl, p)), p);
+    if constexpr (PATH == kPathRow) return S::template load<L, i>(base + x_row_offset<L, i>(cl, p), p);
     else return S::template load<L, i>(src + pull_index<L, i, GENERAL>(cl, p), p);
   };
   auto store = [&](auto I, A v) {

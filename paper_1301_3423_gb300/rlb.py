@@ -18,7 +18,7 @@ STATUS_NAMES = ["RLB_OK", "RLB_EINVAL", "RLB_ENOMEM", "RLB_ECUDA", "RLB_ENONCONV
 STORAGE = {"f64": 0, "f32": 1, "f16dev": 2}
 MAX_VARIANTS = 8
 VARIANT_NAMES = ["registers/scalar", "registers/paired", "registers(168)/scalar", "registers(168)/paired"]
-BC = {"periodic": 0, "copyout": 1}
+BC = {"periodic": 0, "copyout": 1, "bounceback": 2}
 
 
 class RLBError(RuntimeError):

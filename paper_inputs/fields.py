@@ -12,6 +12,17 @@ def riemann_tube(nz, T_left=1.0, T_right=0.5, ny=1, nx=1):
     return T ** 3, T, np.zeros((3, nz, ny, nx))
 
 
+def mirrored_riemann_tube(nz=1600, T_ref=1.0, ny=1, nx=1):
+    """The shock tube of Sec. III as the paper runs it: a periodic tube of nz cells holding the
+    tube and its mirror image, hot (T_ref) for z < nz/4 and z >= 3nz/4, cold (T_ref / 2) between,
+    n = T^3, fluid at rest.  The two discontinuities sit at nz/4 and 3nz/4; the state is symmetric
+    under z -> nz - 1 - z."""
+    z = np.arange(nz)
+    hot = (z < nz // 4) | (z >= nz - nz // 4)
+    T = np.where(hot, T_ref, 0.5 * T_ref)[:, None, None] * np.ones((nz, ny, nx))
+    return T ** 3, T, np.zeros((3, nz, ny, nx))
+
+
 def shear_wave(n_cells, amp=0.05, axis_len=None, ny=None, nz=None):
     """u_y = amp sin(2 pi x / nx) on uniform n = 1, T = 1 (transverse shear wave)."""
     nx = n_cells

@@ -22,6 +22,8 @@ MEMBERS = [
     ((3, 5, 7), (0, 0, 0), 0.1, 29, "random"),
     ((900, 1, 1), (0, 0, 1), 0.5, 41, "tube"),
     ((16, 40, 72), (1, 0, 0), 0.1, 17, "random"),
+    ((24, 16, 48), (2, 0, 2), 0.1, 13, "random"),
+    ((600, 1, 1), (0, 0, 2), 0.1, 19, "tube"),
 ]
 
 

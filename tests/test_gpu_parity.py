@@ -48,7 +48,8 @@ def near_equilibrium(lat, shape, seed, amp=0.02, vmax=0.4, bc=(0, 0, 0)):
     return o.f + amp * (lat.w[:, None, None, None] * n[None] / 2) * rng.standard_normal(o.f.shape)
 
 
-BCS = {"periodic": (0, 0, 0), "copyout_z": (0, 0, 1), "copyout_xy": (1, 1, 0)}
+BCS = {"periodic": (0, 0, 0), "copyout_z": (0, 0, 1), "copyout_xy": (1, 1, 0), "walls_xz": (2, 0, 2),
+       "box": (2, 2, 2)}
 
 
 @pytest.mark.parametrize("order", [3, 2])
@@ -71,7 +72,7 @@ def test_init_matches_oracle(order):
 
 
 @pytest.mark.parametrize("order", [3, 2])
-@pytest.mark.parametrize("bc", ["periodic", "copyout_z", "copyout_xy"])
+@pytest.mark.parametrize("bc", ["periodic", "copyout_z", "copyout_xy", "walls_xz", "box"])
 def test_f64_steps_match_oracle(order, bc):
     """17 x 13 x 11 cells: 19 blocks of 128 threads with a ragged last block; interior warps take
     the constant-offset pull, boundary warps the wrapped / clamped one."""
@@ -113,12 +114,12 @@ def test_f64_interior_warps_match_oracle(order):
 
 @pytest.mark.parametrize("order", [3, 2])
 @pytest.mark.parametrize("variant", [-1, 3])
-@pytest.mark.parametrize("bc", ["periodic", "copyout_xy"])
+@pytest.mark.parametrize("bc", ["periodic", "copyout_xy", "walls_xz"])
 def test_interior_and_shell_kernels_match_oracle(order, variant, bc):
     """72 x 20 x 24 cells.  The row kernel takes the rows with interior y and z in x segments
     [0, 32) (x wraps), [32, 64) (constant offsets) and [64, 72) (partial warp, x wraps); the shell
     kernel the z-boundary planes and y-boundary rows (every coordinate wraps, or x and y are
-    clamped for copy-out).  Double storage per population; float storage (variant 3) on the fields."""
+    clamped for copy-out, or populations from beyond the x and z walls bounce back).  Double storage per population; float storage (variant 3) on the fields."""
     lat = oracle.read_lattice(order)
     shape = (24, 20, 72)
     n, T, u = gen.smooth_random_fields(shape, seed=51, vmax=0.45, sigma_lnT=0.15, kmax=2)
@@ -292,11 +293,14 @@ def test_landau_failure_is_reported_not_hidden():
         assert np.array_equal(g.populations()[0], single[0])  # streamed, not collided
 
 
-@pytest.mark.parametrize("storage,tol,variant", [("f64", 1e-12, -1)] + [("f32", 2e-5, v) for v in range(4)] +
-                         [("f16dev", 2e-2, v) for v in (0, 3)])
-def test_full_size_sampled_cells(storage, tol, variant):
+@pytest.mark.parametrize("storage,tol,variant,bc", [("f64", 1e-12, -1, "periodic")] +
+                         [("f32", 2e-5, v, "periodic") for v in range(4)] +
+                         [("f16dev", 2e-2, v, "periodic") for v in (0, 3)] +
+                         [("f64", 1e-12, -1, "box"), ("f32", 2e-5, 3, "box")])
+def test_full_size_sampled_cells(storage, tol, variant, bc):
     """256^3 random-field case in the benchmark's launch configuration: one step from the seeded
-    equilibrium, 96 cells (corners, faces, interior, random) against the oracle cell by cell."""
+    equilibrium, 96 cells (corners, faces, interior, random) against the oracle cell by cell; also
+    with bounce-back walls on every face."""
     lat = oracle.read_lattice(3)
     N = 256
     shape = (N, N, N)
@@ -305,9 +309,9 @@ def test_full_size_sampled_cells(storage, tol, variant):
     pts = [(0, 0, 0), (N - 1, N - 1, N - 1), (0, N // 2, 5), (N - 1, 3, N - 2), (7, 7, 7), (N // 2, N // 2, N // 2)]
     flat = [x + N * (y + N * z) for z, y, x in pts] + list(rng.integers(0, N ** 3, size=90))
     sample = np.array(flat, dtype=np.int64)
-    o = oracle.OracleRLB(lat, N, N, N, eta_over_s=0.1)
+    o = oracle.OracleRLB(lat, N, N, N, bc=BCS[bc], eta_over_s=0.1)
     ref = o.init_step_cells(n, T, u, sample)
-    with RLB(shape, order=3, storage=storage, eta_over_s=0.1, step_variant=variant) as g:
+    with RLB(shape, order=3, bc=BCS[bc], storage=storage, eta_over_s=0.1, step_variant=variant) as g:
         g.init(n, T, u)
         g.step(1)
         dev = torch.empty((lat.q, N ** 3), dtype=torch.float64, device="cuda")
@@ -316,5 +320,5 @@ def test_full_size_sampled_cells(storage, tol, variant):
         del dev
     scale = np.maximum(np.abs(ref), lat.w[None, :] * n.max() / 2)
     err = float(np.max(np.abs(got - ref) / scale))
-    print("full-size %s variant %d sampled error %.2e" % (storage, variant, err))
+    print("full-size %s variant %d %s sampled error %.2e" % (storage, variant, bc, err))
     assert err < tol

@@ -1,0 +1,97 @@
+"""The paper's workloads on the GPU: the mirrored shock tube of Sec. III with its reference
+temperature scan, and the 128^3 shear wave, each against the FP64 oracle."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_inputs import fields as gen
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU containers
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1301_3423_gb300 import RLB  # noqa: E402
+
+PAPER = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+def steps_to(order, t_fm):
+    dt = PAPER["time_step_fm"]["third_order" if order == 3 else "second_order"]
+    return int(round(t_fm / dt))
+
+
+def pop_err(lat, f, ref, nmax):
+    scale = np.maximum(np.abs(ref), lat.w[:, None, None, None] * nmax / 2)
+    return float(np.max(np.abs(f - ref) / scale))
+
+
+@pytest.mark.parametrize("order", [3, 2])
+@pytest.mark.parametrize("eta_over_s,T_ref", [(0.1, 1.0), (0.5, 1.0), (0.5, 2.5)])
+def test_mirrored_riemann_matches_oracle(order, eta_over_s, T_ref):
+    """1600-cell periodic tube holding the shock tube and its mirror (Sec. III), run to
+    t = 3.2 fm/c in double precision: every population within 1e-12 of the oracle, and u_z odd /
+    n even under z -> 1599 - z to round-off."""
+    lat = oracle.read_lattice(order)
+    nz = PAPER["mirrored_riemann"]["nz_full"]
+    k = steps_to(order, PAPER["mirrored_riemann"]["t_fm"])
+    n, T, u = gen.mirrored_riemann_tube(nz, T_ref)
+    o = oracle.OracleRLB(lat, 1, 1, nz, eta_over_s=eta_over_s)
+    o.init(n, T, u)
+    o.step(k)
+    with RLB((nz, 1, 1), order=order, eta_over_s=eta_over_s) as g:
+        g.init(n, T, u)
+        g.step(k)
+        f = g.populations()
+        m = g.moments()
+    assert o.nonconv == 0
+    assert pop_err(lat, f, o.f, n.max()) < 1e-12
+    vz = m["U"][3, :, 0, 0] / m["U"][0, :, 0, 0]
+    assert np.max(np.abs(vz + vz[::-1])) < 1e-13
+    assert np.max(np.abs(m["n"][:, 0, 0] - m["n"][::-1, 0, 0])) < 1e-13 * m["n"].max()
+
+
+# (steps, sampling interval) per eta/s: the k = 1 mode decays by about 0.011, 0.11 and 0.57 per step,
+# so the runs stop before it reaches the float round-off floor
+SHEAR_RUNS = {0.01: (120, 20), 0.1: (60, 10), 0.5: (18, 3)}
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5)])
+@pytest.mark.parametrize("eta_over_s", sorted(SHEAR_RUNS))
+def test_shear_wave_128_cube_equals_the_1d_oracle(storage, tol, eta_over_s):
+    """The 128^3 shear wave (u_y = 0.05 sin(2 pi x / 128) on n = T = 1, periodic) depends on x only,
+    so every (y, z) row of the GPU lattice must follow the oracle's 128 x 1 x 1 run of the same wave:
+    Landau fields of all 16384 rows against the oracle at every sample, in double (1e-12) and in
+    float storage (1e-5, u relative to the wave's amplitude), and the fitted decay rate of the k = 1
+    mode within 1e-3 of the oracle's."""
+    N = 128
+    steps, every = SHEAR_RUNS[eta_over_s]
+    lat = oracle.read_lattice(3)
+    n1, T1, u1 = gen.shear_wave(N, amp=0.05, ny=1, nz=1)
+    o = oracle.OracleRLB(lat, N, 1, 1, eta_over_s=eta_over_s)
+    o.init(n1, T1, u1)
+    n3, T3, u3 = gen.shear_wave(N, amp=0.05)
+    amp_o, amp_g = [], []
+    with RLB((N, N, N), order=3, storage=storage, eta_over_s=eta_over_s) as g:
+        g.init(n3, T3, u3)
+        for t in range(0, steps + 1, every):
+            if t:
+                o.step(every)
+                g.step(every)
+            ro = o.moments()
+            rg = g.moments()
+            uy_o = ro[2][2, 0, 0, :] / ro[2][0, 0, 0, :]
+            uy_g = rg["U"][2] / rg["U"][0]
+            assert np.max(np.abs(uy_g - uy_o[None, None, :])) <= tol * 0.05, t
+            assert np.max(np.abs(rg["n"] - ro[0][0, 0, :][None, None, :])) <= tol, t
+            amp_o.append(abs(np.fft.rfft(uy_o)[1]))
+            amp_g.append(abs(np.fft.rfft(uy_g[N // 3, N // 5])[1]))
+    ts = np.arange(0, steps + 1, every)
+    rate_o = -np.polyfit(ts[1:], np.log(amp_o[1:]), 1)[0]
+    rate_g = -np.polyfit(ts[1:], np.log(amp_g[1:]), 1)[0]
+    print("shear %s eta/s %.2f: decay per step oracle %.6e gpu %.6e" % (storage, eta_over_s, rate_o, rate_g))
+    assert rate_o > 0 and abs(rate_g - rate_o) <= 1e-3 * rate_o
