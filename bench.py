@@ -200,10 +200,12 @@ def batched_instances(scale, seed=4, count=64):
     return out
 
 
-def make_instance(spec, storage, variant=-1, stream=None):
+def make_instance(spec, storage, variant=-1, stream=None, landau_fp64=False):
+    """One instance of the batched workload.  Float storage solves Landau matching in float with a
+    double solve for cells above gamma_thr; landau_fp64=True solves every cell in double."""
     from paper_1301_3423_gb300 import RLB
     kind, shape, bc, eta, steps, seed = spec
-    c = RLB(shape, order=ORDER, bc=bc, eta_over_s=eta, storage=storage, landau_fp64=(storage != "f64"),
+    c = RLB(shape, order=ORDER, bc=bc, eta_over_s=eta, storage=storage, landau_fp64=landau_fp64,
             step_variant=variant, stream=stream)
     if kind == "tube":
         f = gen.riemann_tube(shape[0])
@@ -223,23 +225,32 @@ def run_batched(args, stream):
     from paper_1301_3423_gb300 import Batch
     specs = batched_instances(args.batch_scale)
     updates = float(sum(np.prod(sp[1]) * sp[4] for sp in specs))
-    ctxs = [make_instance(sp, "f32", stream=stream) for sp in specs]
-    b = Batch(ORDER, "f32", stream=stream)
-    for c, sp in zip(ctxs, specs):
-        b.add(c, sp[4])
-    variant, _ = b.autotune(reps=2)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    active = len(ctxs)
-    while active:
-        active = b.run(25, graph=True)
-    torch.cuda.synchronize()
-    t_batch = time.perf_counter() - t0
-    for c in ctxs:
-        c.sync()
-        c.close()
-    launches = b.kernel_launches
-    b.close()
+
+    def batched_run(landau_fp64, variant=None):
+        ctxs = [make_instance(sp, "f32", stream=stream, landau_fp64=landau_fp64) for sp in specs]
+        b = Batch(ORDER, "f32", stream=stream)
+        for c, sp in zip(ctxs, specs):
+            b.add(c, sp[4])
+        if variant is None:
+            variant, _ = b.autotune(reps=2)
+        else:
+            b.set_variant(variant)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        active = len(ctxs)
+        while active:
+            active = b.run(25, graph=True)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        for c in ctxs:
+            c.sync()
+            c.close()
+        launches = b.kernel_launches
+        b.close()
+        return t, variant, launches
+
+    t_batch, variant, launches = batched_run(False)
+    t_batch_d, _, _ = batched_run(True, variant)
     t_seq = 0.0  # only the stepping counts, as for the batch
     for sp in specs:
         c = make_instance(sp, "f32", variant=variant, stream=stream)
@@ -263,6 +274,9 @@ def run_batched(args, stream):
     return {"instances": len(specs), "cell_updates": updates, "step_scale": args.batch_scale,
             "value": updates / t_batch / 1e6, "unit": "MLUPS", "seconds": t_batch, "solves_per_s": len(specs) / t_batch,
             "variant": variant, "kernel_launches": launches, "graph_steps": 25,
+            "landau": "float, double above gamma_thr = 2",
+            "fp64_landau_every_cell": {"value": updates / t_batch_d / 1e6, "seconds": t_batch_d,
+                                       "solves_per_s": len(specs) / t_batch_d},
             "sequential_f32": {"value": updates / t_seq / 1e6, "seconds": t_seq, "solves_per_s": len(specs) / t_seq},
             "fp64_plain": {"value": u64 / t64 / 1e6, "instances": len(sub), "seconds": t64,
                            "solves_per_s_est": len(specs) / (t64 * updates / u64)}}

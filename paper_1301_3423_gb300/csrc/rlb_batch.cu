@@ -25,7 +25,7 @@ struct Member {
 struct GraphCache {
   cudaGraphExec_t exec = nullptr;
   long nsteps = 0, version = -1;
-  int variant = -1, nmembers = 0, tiles = 0;
+  int variant = -1, nmembers = 0, tiles = 0, walls = -1;
 };
 
 }  // namespace
@@ -40,6 +40,7 @@ struct rlb_batch {
   long counters_capacity = 0;
   const Launchers* launch = nullptr;
   int variant = 0;
+  int walls = 0;                 // some member of the uploaded table has bounce-back walls
   int sms = 0;
   long version = 0;              // bumps when the member set changes
   long launches = 0;
@@ -122,6 +123,7 @@ extern "C" long rlb_batch_steps_left(const rlb_batch* b, int slot) {
 static rlb_status upload_table(rlb_batch* b, long nsteps, int* nmembers, int* total_tiles) {
   std::vector<BatchMember> t;
   int tiles = 0;
+  b->walls = 0;
   for (const Member& m : b->members) {
     if (!m.ctx || m.steps_left <= 0) continue;
     BatchMember d{};
@@ -132,7 +134,9 @@ static rlb_status upload_table(rlb_batch* b, long nsteps, int* nmembers, int* to
     d.parity0 = m.ctx->cur;
     d.steps_left = (int)std::min<long>(m.steps_left, nsteps);
     d.tile_begin = tiles;
-    tiles += (m.ctx->cells + kStepThreads - 1) / kStepThreads;
+    if (d.p.has_wall) b->walls = 1;
+    d.int_tiles = (d.p.int_warps + kStepThreads / 32 - 1) / (kStepThreads / 32);
+    tiles += d.int_tiles + (d.p.shell_cells + kStepThreads - 1) / kStepThreads;
     t.push_back(d);
   }
   *nmembers = (int)t.size();
@@ -177,7 +181,8 @@ static rlb_status enqueue_run(rlb_batch* b, long nsteps, int nmem, int tiles, in
   BATCH_CUDA(b, cudaMemsetAsync(b->d_counters, 0, (size_t)nsteps * sizeof(int), b->stream));
   const int grid = grid_of(b, variant);
   for (long k = 0; k < nsteps; ++k) {
-    cudaError_t e = b->launch->batch_step(b->d_members, nmem, tiles, (int)k, b->d_counters, variant, grid, b->stream);
+    cudaError_t e =
+        b->launch->batch_step(b->d_members, nmem, tiles, (int)k, b->d_counters, variant, b->walls, grid, b->stream);
     ++b->launches;
     if (e != cudaSuccess) return bfail(b, RLB_ECUDA, std::string("batched step: ") + cudaGetErrorString(e));
   }
@@ -204,7 +209,7 @@ extern "C" rlb_status rlb_batch_run(rlb_batch* b, long nsteps, int use_graph, in
       // members' tile count stay the same
       GraphCache& gc = b->graph;
       if (!gc.exec || gc.nsteps != nsteps || gc.version != b->version || gc.variant != b->variant ||
-          gc.nmembers != nmem || gc.tiles != tiles) {
+          gc.nmembers != nmem || gc.tiles != tiles || gc.walls != b->walls) {
         if (b->graph.exec) cudaGraphExecDestroy(b->graph.exec);
         b->graph.exec = nullptr;
         cudaStream_t cs;
@@ -232,6 +237,7 @@ extern "C" rlb_status rlb_batch_run(rlb_batch* b, long nsteps, int use_graph, in
         gc.variant = b->variant;
         gc.nmembers = nmem;
         gc.tiles = tiles;
+        gc.walls = b->walls;
       }
       BATCH_CUDA(b, cudaGraphLaunch(b->graph.exec, b->stream));
       b->launches += nsteps;
@@ -281,7 +287,8 @@ extern "C" rlb_status rlb_batch_autotune(rlb_batch* b, int reps, int* variant, d
       for (int r = 0; r <= reps; ++r) {
         if (r == 1) BATCH_CUDA(b, cudaEventRecord(e0, b->stream));
         // every repetition is launch 0 of the same run: the same next state into the spare buffers
-        cudaError_t e = b->launch->batch_step(b->d_members, nmem, tiles, 0, b->d_counters + r, v, grid, b->stream);
+        cudaError_t e =
+            b->launch->batch_step(b->d_members, nmem, tiles, 0, b->d_counters + r, v, b->walls, grid, b->stream);
         if (e != cudaSuccess) return bfail(b, RLB_ECUDA, std::string("batched step: ") + cudaGetErrorString(e));
       }
       BATCH_CUDA(b, cudaEventRecord(e1, b->stream));

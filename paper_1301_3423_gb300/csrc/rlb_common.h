@@ -47,7 +47,8 @@ struct BatchMember {
   int parity0;        // buffer holding the state before launch 0 of this run
   int steps_left;     // launches with index >= steps_left leave this member alone
   int tile_begin;     // first tile of this member in the queue
-  int pad;
+  int int_tiles;      // its first int_tiles tiles are row tiles (4 row-kernel warps), the rest shell
+                      // tiles (kStepThreads shell cells)
 };
 
 }  // namespace rlb

@@ -10,32 +10,43 @@ namespace rlb {
 using namespace inst;
 constexpr int V = RLB_INST_VARIANT;
 
-// One time step = the interior kernel plus the shell kernel (disjoint cells, same source).
-cudaError_t RLB_VFN(step, RLB_INST_VARIANT)(const void* src, void* dst, const StepParams& p, int* status,
-                                            bool general, cudaStream_t s) {
+namespace {
+template <bool W>
+void launch_step(const void* src, void* dst, const StepParams& p, int* status, bool general, cudaStream_t s) {
   if (p.int_warps > 0) {
     const int blocks = (p.int_warps + kStepThreads / 32 - 1) / (kStepThreads / 32);
-    k_step_interior<L, S, V><<<blocks, kStepThreads, 0, s>>>((const T*)src, (T*)dst, p, status);
+    k_step_interior<L, S, V, W><<<blocks, kStepThreads, 0, s>>>((const T*)src, (T*)dst, p, status);
   }
   if (p.shell_cells > 0) {
     const int blocks = (p.shell_cells + kStepThreads - 1) / kStepThreads;
     if (general)
-      k_step_shell<L, S, true, V><<<blocks, kStepThreads, 0, s>>>((const T*)src, (T*)dst, p, status);
+      k_step_shell<L, S, true, V, W><<<blocks, kStepThreads, 0, s>>>((const T*)src, (T*)dst, p, status);
     else
-      k_step_shell<L, S, false, V><<<blocks, kStepThreads, 0, s>>>((const T*)src, (T*)dst, p, status);
+      k_step_shell<L, S, false, V, W><<<blocks, kStepThreads, 0, s>>>((const T*)src, (T*)dst, p, status);
   }
+}
+}  // namespace
+
+// One time step = the interior kernel plus the shell kernel (disjoint cells, same source), compiled
+// with the bounce-back test only for lattices that have walls.
+cudaError_t RLB_VFN(step, RLB_INST_VARIANT)(const void* src, void* dst, const StepParams& p, int* status,
+                                            bool general, cudaStream_t s) {
+  if (p.has_wall) launch_step<true>(src, dst, p, status, general, s);
+  else launch_step<false>(src, dst, p, status, general, s);
   return cudaGetLastError();
 }
 
-cudaError_t RLB_VFN(batch, RLB_INST_VARIANT)(const BatchMember* m, int n, int tiles, int li, int* counters, int grid,
-                                             cudaStream_t s) {
-  k_step_batch<L, S, V><<<grid, kStepThreads, 0, s>>>(m, n, tiles, li, counters);
+cudaError_t RLB_VFN(batch, RLB_INST_VARIANT)(const BatchMember* m, int n, int tiles, int li, int* counters, int walls,
+                                             int grid, cudaStream_t s) {
+  if (walls) k_step_batch<L, S, V, true><<<grid, kStepThreads, 0, s>>>(m, n, tiles, li, counters);
+  else k_step_batch<L, S, V, false><<<grid, kStepThreads, 0, s>>>(m, n, tiles, li, counters);
   return cudaGetLastError();
 }
 
 int RLB_VFN(occupancy, RLB_INST_VARIANT)() {
-  int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_batch<L, S, V>, kStepThreads, 0) != cudaSuccess) {
+  int nb = 0;  // both instantiations have the same launch bounds
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_batch<L, S, V, false>, kStepThreads, 0) !=
+      cudaSuccess) {
     cudaGetLastError();
     return 1;
   }

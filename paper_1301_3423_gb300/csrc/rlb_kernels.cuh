@@ -144,29 +144,27 @@ __device__ __forceinline__ bool beyond_wall(const Cell& cl, const StepParams& p)
   return b;
 }
 
-template <class L, int I, bool GENERAL>
+// WALLS = false compiles the bounce-back test out: kernels for lattices without walls pay nothing.
+template <class L, int I, bool GENERAL, bool WALLS>
 __device__ __forceinline__ long long pull_index(const Cell& cl, const StepParams& p) {
   constexpr int vx = L::VX[I], vy = L::VY[I], vz = L::VZ[I];
-  if (p.has_wall && beyond_wall<L, I>(cl, p)) return (long long)(I ^ 1) * p.cells + cl.c;
+  if constexpr (WALLS) {
+    if (p.has_wall && beyond_wall<L, I>(cl, p)) return (long long)(I ^ 1) * p.cells + cl.c;
+  }
   const int sx = src_coord<vx, GENERAL>(cl.x, p.nx, p.bc[0]);
   const int sy = src_coord<vy, GENERAL>(cl.y, p.ny, p.bc[1]);
   const int sz = src_coord<vz, GENERAL>(cl.z, p.nz, p.bc[2]);
   return (long long)I * p.cells + (long long)(sz * p.nxy + sy * p.nx + sx);
 }
 
-template <class L>
-__device__ __forceinline__ bool is_interior(const Cell& cl, const StepParams& p) {
-  return cl.x >= L::VMAX_X && cl.x < p.nx - L::VMAX_X && cl.y >= L::VMAX_Y && cl.y < p.ny - L::VMAX_Y &&
-         cl.z >= L::VMAX_Z && cl.z < p.nz - L::VMAX_Z;
-}
 
 // Pull offset of population I from the cell's own index when only the x coordinate can leave the
 // lattice (rows whose y and z are interior): the constant offset with x wrapped or clamped, or the
 // cell's own reversed population beyond a bounce-back wall in x.
-template <class L, int I>
+template <class L, int I, bool WALLS>
 __device__ __forceinline__ long long x_row_offset(const Cell& cl, const StepParams& p) {
   constexpr int vx = L::VX[I];
-  if constexpr (vx != 0) {
+  if constexpr (WALLS && vx != 0) {
     if (p.bc[0] == kBounceBack && (unsigned)(cl.x - vx) >= (unsigned)p.nx) return (long long)(I ^ 1) * p.cells;
   }
   return p.off[I] + (src_coord<vx, false>(cl.x, p.nx, p.bc[0]) - (cl.x - vx));
@@ -254,16 +252,12 @@ struct Landau {
   bool ok;
 };
 
-template <class A, int MAXIT, bool EARLY>
-__device__ __forceinline__ Landau<A> landau(const Mom<A>& m) {
+// Shifted power iteration from the start vector (U0, Ux, Uy, Uz), at most MAXIT updates; a lane
+// stops once an update moves U by at most tol * U0.
+template <class A, int MAXIT>
+__device__ __forceinline__ Landau<A> landau_from(const Mom<A>& m, A U0, A Ux, A Uy, A Uz, const A tol) {
   Landau<A> r;
   r.ok = false;
-  const A NN = m.N0 * m.N0 - m.Nx * m.Nx - m.Ny * m.Ny - m.Nz * m.Nz;
-  if (!(NN > A(0)) || !(m.N0 > A(0))) return r;
-  A is = rsqrt_(NN);
-  A U0 = m.N0 * is, Ux = m.Nx * is, Uy = m.Ny * is, Uz = m.Nz * is;
-  // stop when an update moves U by less than a few units in the last place of U0
-  const A tol = std::is_same<A, double>::value ? A(8e-16) : A(3e-7);
   for (int it = 0; it < MAXIT; ++it) {
     const A V0 = m.T00 * U0 - m.T0x * Ux - m.T0y * Uy - m.T0z * Uz;
     const A Vx = m.T0x * U0 - m.Txx * Ux - m.Txy * Uy - m.Txz * Uz;
@@ -275,13 +269,9 @@ __device__ __forceinline__ Landau<A> landau(const Mom<A>& m) {
     if (!(WW > A(0)) || !(W0 > A(0))) return r;
     const A iw = rsqrt_(WW);
     const A n0 = W0 * iw, nx = Wx * iw, ny = Wy * iw, nz = Wz * iw;
-    if constexpr (EARLY) {
-      const A d = fmax(fmax(fabs(n0 - U0), fabs(nx - Ux)), fmax(fabs(ny - Uy), fabs(nz - Uz)));
-      U0 = n0; Ux = nx; Uy = ny; Uz = nz;
-      if (d <= tol * U0) break;
-    } else {
-      U0 = n0; Ux = nx; Uy = ny; Uz = nz;
-    }
+    const A d = fmax(fmax(fabs(n0 - U0), fabs(nx - Ux)), fmax(fabs(ny - Uy), fabs(nz - Uz)));
+    U0 = n0; Ux = nx; Uy = ny; Uz = nz;
+    if (d <= tol * U0) break;
   }
   const A V0 = m.T00 * U0 - m.T0x * Ux - m.T0y * Uy - m.T0z * Uz;
   const A Vx = m.T0x * U0 - m.Txx * Ux - m.Txy * Uy - m.Txz * Uz;
@@ -294,10 +284,35 @@ __device__ __forceinline__ Landau<A> landau(const Mom<A>& m) {
   return r;
 }
 
+// Landau matching from the Eckart vector N / |N|; double stops at 8e-16 U0 (a few units in the last
+// place), float at 3e-7 U0.
+template <class A, int MAXIT>
+__device__ __forceinline__ Landau<A> landau(const Mom<A>& m) {
+  const A NN = m.N0 * m.N0 - m.Nx * m.Nx - m.Ny * m.Ny - m.Nz * m.Nz;
+  if (!(NN > A(0)) || !(m.N0 > A(0))) {
+    Landau<A> r;
+    r.ok = false;
+    return r;
+  }
+  const A is = rsqrt_(NN);
+  const A tol = std::is_same<A, double>::value ? A(8e-16) : A(3e-7);
+  return landau_from<A, MAXIT>(m, m.N0 * is, m.Nx * is, m.Ny * is, m.Nz * is, tol);
+}
+
 // The double-precision solve of a float step, kept out of line: it runs for few cells and would
-// otherwise grow the step kernel's hot code.
+// otherwise grow the step kernel's hot code (a call keeps the caller's register allocation that of
+// the float path).  It starts from the Eckart vector and stops at 1e-12 U0: the populations are
+// float, so more digits carry no information, while the double arithmetic still removes the
+// gamma^2 cancellation in U.U = 1.
 static __device__ __noinline__ Landau<double> landau_fp64_out_of_line(const Mom<double> m) {
-  return landau<double, 40, true>(m);
+  const double NN = m.N0 * m.N0 - m.Nx * m.Nx - m.Ny * m.Ny - m.Nz * m.Nz;
+  if (!(NN > 0.0) || !(m.N0 > 0.0)) {
+    Landau<double> r;
+    r.ok = false;
+    return r;
+  }
+  const double is = rsqrt(NN);
+  return landau_from<double, 40>(m, m.N0 * is, m.Nx * is, m.Ny * is, m.Nz * is, 1e-12);
 }
 
 // Landau matching in the step's arithmetic A.  Reduced-precision paths switch to double for cells
@@ -306,14 +321,14 @@ static __device__ __noinline__ Landau<double> landau_fp64_out_of_line(const Mom<
 template <class A>
 __device__ __forceinline__ Landau<A> landau_step(const Mom<A>& m, const StepParams& p) {
   if constexpr (std::is_same<A, double>::value) {
-    return landau<double, 40, true>(m);
+    return landau<double, 40>(m);
   } else {
     const float NN = m.N0 * m.N0 - m.Nx * m.Nx - m.Ny * m.Ny - m.Nz * m.Nz;
     if (p.landau_fp64 || m.N0 * m.N0 > p.gamma_thr2 * NN) {
       const Landau<double> d = landau_fp64_out_of_line(convert<A, double>(m));
       return Landau<A>{(A)d.U0, (A)d.Ux, (A)d.Uy, (A)d.Uz, (A)d.eps, (A)d.n, d.ok};
     }
-    return landau<float, 8, true>(m);
+    return landau<float, 8>(m);
   }
 }
 
@@ -579,15 +594,14 @@ struct StepShape {
   static constexpr int kMinBlocks = (VARIANT & 2) ? 3 : 1;
 };
 
-// How a step kernel pulls: kPathAuto lets each warp vote (all lanes interior: constant offsets,
-// else wrapped / clamped indices); the row kernel's warps lie in rows with interior y and z and
-// are told whether their x segment is interior too (else only x wraps); the shell kernel wraps
-// every coordinate.
-enum PullPath : int { kPathAuto = 0, kPathRow = 1, kPathEdge = 2 };
+// How a step kernel pulls: the row kernel's warps lie in rows with interior y and z and are told
+// whether their x segment is interior too (constant offsets) or not (only x wraps); the shell
+// kernel wraps every coordinate.
+enum PullPath : int { kPathRow = 1, kPathEdge = 2 };
 
 // One cell's time step (pull, moments, Landau matching, equilibrium, collision, store).  Invalid
 // lanes (valid = false) carry a clamped in-range cell, compute and store nothing.
-template <class L, class S, bool GENERAL, int VARIANT, int PATH>
+template <class L, class S, bool GENERAL, int VARIANT, int PATH, bool WALLS>
 __device__ __forceinline__ void step_cell(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
                                           const StepParams& p, int* __restrict__ status, const Cell cl,
                                           const bool valid, const bool row_fast = false) {
@@ -595,20 +609,18 @@ __device__ __forceinline__ void step_cell(const typename S::T* __restrict__ src,
   using ST = typename S::T;
   constexpr bool PACKED = (VARIANT & 1) && std::is_same<A, float>::value;
   constexpr bool KEEP = StepShape<S, VARIANT>::kKeep;
-  // Warp-uniform choice: if every lane's stencil stays inside the lattice, pull with constant
-  // offsets; otherwise resolve periodic wrap / copy-out per population.
-  bool fast;
-  if constexpr (PATH == kPathRow) fast = row_fast;
-  else if constexpr (PATH == kPathEdge) fast = false;
-  else fast = __all_sync(0xffffffffu, is_interior<L>(cl, p));
+  // Warp-uniform choice: a row warp whose segment is interior pulls with constant offsets; other
+  // row warps wrap x only; shell cells resolve wrap / copy-out / bounce-back per population.
+  static_assert(PATH == kPathRow || PATH == kPathEdge, "pull path");
+  const bool fast = PATH == kPathRow && row_fast;
   const ST* __restrict__ base = src + cl.c;
   ST* __restrict__ out = dst + cl.c;
 
   auto load = [&](auto I) -> A {
     constexpr int i = decltype(I)::value;
     if (fast) return S::template load<L, i>(base + p.off[i], p);
-    if constexpr (PATH == kPathRow) return S::template load<L, i>(base + x_row_offset<L, i>(cl, p), p);
-    else return S::template load<L, i>(src + pull_index<L, i, GENERAL>(cl, p), p);
+    if constexpr (PATH == kPathRow) return S::template load<L, i>(base + x_row_offset<L, i, WALLS>(cl, p), p);
+    else return S::template load<L, i>(src + pull_index<L, i, GENERAL, WALLS>(cl, p), p);
   };
   auto store = [&](auto I, A v) {
     constexpr int i = decltype(I)::value;
@@ -673,7 +685,7 @@ __device__ __forceinline__ void row_cell(int w, int lane, const StepParams& p, C
 // w % int_segs of row w / int_segs (the last segment may be partial).  A segment inside the
 // interior x range pulls with constant offsets; the others wrap only x.  Whole rows in one kernel
 // keep every sector of a row written by neighbouring warps.
-template <class L, class S, int VARIANT>
+template <class L, class S, int VARIANT, bool WALLS>
 __global__ void __launch_bounds__(kStepThreads, StepShape<S, VARIANT>::kMinBlocks)
     k_step_interior(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
                     const __grid_constant__ StepParams p, int* __restrict__ status) {
@@ -682,7 +694,7 @@ __global__ void __launch_bounds__(kStepThreads, StepShape<S, VARIANT>::kMinBlock
   Cell cl;
   bool valid, fast;
   row_cell(w, threadIdx.x & 31, p, cl, valid, fast);
-  step_cell<L, S, false, VARIANT, kPathRow>(src, dst, p, status, cl, valid, fast);
+  step_cell<L, S, false, VARIANT, kPathRow, WALLS>(src, dst, p, status, cl, valid, fast);
 }
 
 // Shell cells (rows whose y or z lies outside the interior box): z-boundary planes, then the
@@ -708,27 +720,27 @@ __device__ __forceinline__ Cell shell_cell(int s, const StepParams& p) {
   return cl;
 }
 
-template <class L, class S, bool GENERAL, int VARIANT>
+template <class L, class S, bool GENERAL, int VARIANT, bool WALLS>
 __global__ void __launch_bounds__(kStepThreads, StepShape<S, VARIANT>::kMinBlocks)
     k_step_shell(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
                  const __grid_constant__ StepParams p, int* __restrict__ status) {
   const int s = blockIdx.x * kStepThreads + threadIdx.x;
   const bool valid = s < p.shell_cells;
   const Cell cl = shell_cell(valid ? s : p.shell_cells - 1, p);
-  step_cell<L, S, GENERAL, VARIANT, kPathEdge>(src, dst, p, status, cl, valid);
+  step_cell<L, S, GENERAL, VARIANT, kPathEdge, WALLS>(src, dst, p, status, cl, valid);
 }
 
 // ---------------------------------------------------------------------------------------------
 // Batched step: many independent lattices (members) advance together.  A persistent grid takes
-// tiles of kStepThreads consecutive cells from one shared queue (an atomic counter per launch);
-// a tile belongs to one member, found by binary search over the members' first tile.  Each
-// launch is one time step of every member whose step count is not yet reached.  The per-cell code
-// and the grouping of cells into warps are those of k_step, so a member's populations are bitwise
-// the same as when it runs alone with the same variant.
+// tiles from one shared queue (an atomic counter per launch); a tile belongs to one member, found
+// by binary search over the members' first tile.  A member's tiles are first its row tiles, four
+// warps of the row kernel's segments each (constant offsets, or x wrapped only), then its shell
+// tiles of kStepThreads shell cells (every coordinate wrapped): the decomposition of a solo step,
+// so a member's populations are bitwise those of the same steps taken alone with the same variant.
+// Each launch is one time step of every member whose step count is not yet reached.
 // ---------------------------------------------------------------------------------------------
 
-
-template <class L, class S, int VARIANT>
+template <class L, class S, int VARIANT, bool WALLS>
 __global__ void __launch_bounds__(kStepThreads, StepShape<S, VARIANT>::kMinBlocks)
     k_step_batch(const BatchMember* __restrict__ members, int nmembers, int total_tiles, int launch_index,
                  int* __restrict__ counters) {
@@ -761,13 +773,24 @@ __global__ void __launch_bounds__(kStepThreads, StepShape<S, VARIANT>::kMinBlock
     __syncthreads();
     if (active) {
       const int par = (m.parity0 + launch_index) & 1;
-      const int gid = (tile - m.tile_begin) * kStepThreads + threadIdx.x;
-      const bool valid = gid < sp.cells;
-      const Cell cl = make_cell(valid ? gid : sp.cells - 1, sp);
+      const int lt = tile - m.tile_begin;
       const ST* sb = static_cast<const ST*>(m.buf[par]);
       ST* db = static_cast<ST*>(m.buf[par ^ 1]);
-      if (sp.general) step_cell<L, S, true, VARIANT, kPathAuto>(sb, db, sp, m.status, cl, valid);
-      else step_cell<L, S, false, VARIANT, kPathAuto>(sb, db, sp, m.status, cl, valid);
+      if (lt < m.int_tiles) {
+        const int w = lt * (kStepThreads / 32) + (threadIdx.x >> 5);
+        if (w < sp.int_warps) {  // whole warps only
+          Cell cl;
+          bool valid, fast;
+          row_cell(w, threadIdx.x & 31, sp, cl, valid, fast);
+          step_cell<L, S, false, VARIANT, kPathRow, WALLS>(sb, db, sp, m.status, cl, valid, fast);
+        }
+      } else {
+        const int s = (lt - m.int_tiles) * kStepThreads + threadIdx.x;
+        const bool valid = s < sp.shell_cells;
+        const Cell cl = shell_cell(valid ? s : sp.shell_cells - 1, sp);
+        if (sp.general) step_cell<L, S, true, VARIANT, kPathEdge, WALLS>(sb, db, sp, m.status, cl, valid);
+        else step_cell<L, S, false, VARIANT, kPathEdge, WALLS>(sb, db, sp, m.status, cl, valid);
+      }
     }
     __syncthreads();  // sp and s_tile are reused by the next tile
   }
@@ -791,11 +814,11 @@ __global__ void __launch_bounds__(kMomThreads) k_fields(const typename S::T* __r
   const Cell cl = make_cell(valid ? gid : p.cells - 1, p);
   auto get = [&](auto I) -> double {
     constexpr int i = decltype(I)::value;
-    const long long idx = PULL ? pull_index<L, i, true>(cl, p) : (long long)i * p.cells + cl.c;
+    const long long idx = PULL ? pull_index<L, i, true, true>(cl, p) : (long long)i * p.cells + cl.c;
     return S::template to_f64<L, i>(src[idx], p);
   };
   const Mom<double> m = moments<L, double>(get);
-  const Landau<double> lw = landau<double, 200, true>(m);
+  const Landau<double> lw = landau<double, 200>(m);
   if (valid) {
     const double nan = __longlong_as_double(0x7ff8000000000000ll);
     fields[0 * (long long)p.cells + cl.c] = lw.ok ? lw.n : nan;

@@ -16,9 +16,10 @@ struct Launchers {
                       cudaStream_t s);
   cudaError_t (*convert)(void* pop, double* dbl, int i0, int i1, bool to_f64, const StepParams& p, cudaStream_t s);
   int step_variants;  // number of step-kernel variants the autotuner may choose from
-  // one launch of the persistent batched step (grid blocks over the shared tile queue)
+  // one launch of the persistent batched step (grid blocks over the shared tile queue); walls != 0
+  // selects the kernel with the bounce-back test (some member has walls)
   cudaError_t (*batch_step)(const BatchMember* members, int nmembers, int total_tiles, int launch_index,
-                            int* counters, int variant, int grid, cudaStream_t s);
+                            int* counters, int variant, int walls, int grid, cudaStream_t s);
   // resident blocks per SM of the batched step for a variant
   int (*batch_blocks_per_sm)(int variant);
 };

@@ -92,8 +92,12 @@ def poisson_requests(n, rate=20.0, seed=0, sizes=(32, 48, 64, 96, 128, 192, 256,
 class Server:
     """Admission against an HBM budget plus continuous batching (see the module docstring)."""
 
-    def __init__(self, order=3, hbm_budget=150e9, chunk=50, use_graph=True, stream=None, autotune=False):
+    def __init__(self, order=3, hbm_budget=150e9, chunk=50, use_graph=True, stream=None, autotune=False,
+                 landau_fp64=False):
+        """landau_fp64: solve Landau matching in double for every cell (default: in float, in double
+        for cells above gamma_thr)."""
         self.order = order
+        self.landau_fp64 = bool(landau_fp64)
         self.budget = float(hbm_budget)
         self.chunk = int(chunk)
         self.use_graph = use_graph
@@ -133,7 +137,7 @@ class Server:
                 break  # first come, first served: wait for memory
             self.waiting.pop(0)
             ctx = RLB(req.shape, order=self.order, bc=req.bc, eta_over_s=req.eta_over_s, storage=req.storage,
-                      landau_fp64=True, stream=self.stream)
+                      landau_fp64=self.landau_fp64, stream=self.stream)
             ctx.init(*initial_fields(req))
             slot = self._batch(req.storage).add(ctx, req.steps)
             self.active[(req.storage, slot)] = (req, ctx, self.now(), need)

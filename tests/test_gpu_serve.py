@@ -12,19 +12,21 @@ from paper_1301_3423_gb300 import RLB  # noqa: E402
 from paper_1301_3423_gb300 import serve  # noqa: E402
 
 
-def solo(req):
-    with RLB(req.shape, order=3, bc=req.bc, eta_over_s=req.eta_over_s, storage=req.storage, landau_fp64=True) as c:
+def solo(req, landau_fp64):
+    with RLB(req.shape, order=3, bc=req.bc, eta_over_s=req.eta_over_s, storage=req.storage,
+             landau_fp64=landau_fp64) as c:
         c.init(*serve.initial_fields(req))
         c.step(req.steps)
         return c.moments()
 
 
-def test_served_results_equal_solo_runs_and_admission_respects_the_budget():
+@pytest.mark.parametrize("landau_fp64", [False, True])
+def test_served_results_equal_solo_runs_and_admission_respects_the_budget(landau_fp64):
     reqs = serve.poisson_requests(12, rate=200.0, seed=3, sizes=(16, 24, 32), step_scale=0.02, f16_fraction=0.3)
     # a budget below the total forces waiting and re-admission
     sizes = [serve.Server.bytes_of(r) for r in reqs]
     budget = max(sizes) + 0.3 * (sum(sizes) - max(sizes))
-    srv = serve.Server(hbm_budget=budget, chunk=7)
+    srv = serve.Server(hbm_budget=budget, chunk=7, landau_fp64=landau_fp64)
     try:
         st = srv.run(reqs, realtime=False)
     finally:
@@ -34,7 +36,7 @@ def test_served_results_equal_solo_runs_and_admission_respects_the_budget():
     assert srv.peak_active < len(reqs)  # not everything fitted at once
     by_id = {r.rid: r for r in srv.results}
     for req in reqs:
-        ref = solo(req)
+        ref = solo(req, landau_fp64)
         got = by_id[req.rid]
         assert got.steps == req.steps
         for key in ("n", "eps", "U", "totals"):
