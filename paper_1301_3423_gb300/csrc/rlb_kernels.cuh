@@ -385,11 +385,48 @@ __device__ __forceinline__ EqCoef<ORDER, A> eq_coef(A n, A T, A U0) {
   return c;
 }
 
+// The equilibrium as a polynomial in t per energy level l (p0 = p0_l):
+//   E(p0_l, t) = a_l + t (b_l + t (c_l + t d_l)),
+//   order 3: a = c00 + p0 c10 + p0^2 c20 + pref p0^3 x^3,  b = p0 c01 + p0^2 c11 + 3 pref p0^3 x^2 T,
+//            c = p0^2 c02 + 3 pref p0^3 x T^2,             d = pref p0^3 T^3;
+//   order 2: a = c00 + p0 c10 + pref p0^2 x^2,  b = p0 c01 + 2 pref p0^2 x T,  c = pref p0^2 T^2,  d = 0.
+// The same regrouping of App. B's forms: the per-cell work moves from the 48 (15) directions to
+// the 4 (3) energy levels, and each population costs a cubic (quadratic) Horner step in t.
+template <class L, class A>
+struct LevCoef {
+  A a[L::NLEV], b[L::NLEV], c[L::NLEV], d[L::NLEV];
+};
+
+template <class L, class A>
+__device__ __forceinline__ LevCoef<L, A> level_coef(const EqCoef<L::ORDER, A>& q) {
+  LevCoef<L, A> r;
+  static_for<L::NLEV>([&](auto K) {
+    constexpr int l = decltype(K)::value;
+    constexpr double pd = L::P0[l];
+    const A p = A(pd), p2 = A(pd * pd);
+    if constexpr (L::ORDER == 3) {
+      const A pp3 = A(pd * pd * pd) * q.pref;  // pref p0^3
+      const A ppx = pp3 * q.x;
+      r.d[l] = pp3 * (q.T * q.T * q.T);
+      r.c[l] = fma(A(3) * ppx, q.T * q.T, p2 * q.c02);
+      r.b[l] = fma(A(3) * ppx * q.x, q.T, fma(p2, q.c11, p * q.c01));
+      r.a[l] = fma(ppx * q.x, q.x, fma(p2, q.c20, fma(p, q.c10, q.c00)));
+    } else {
+      const A pp2 = p2 * q.pref;  // pref p0^2
+      r.d[l] = A(0);
+      r.c[l] = pp2 * (q.T * q.T);
+      r.b[l] = fma(A(2) * pp2 * q.x, q.T, p * q.c01);
+      r.a[l] = fma(pp2 * q.x, q.x, fma(p, q.c10, q.c00));
+    }
+  });
+  return r;
+}
+
 // Collision of one cell (Eq. (rlb:disc) right-hand side, delta t' = 1):
 //   f*_i = f_i + omega_i (w_i E_i - f_i),  omega_i = p_i.U / (tau' p0_i) = (U0 - t_i) / tau'.
 template <class L, class A, class Get, class Put>
 __device__ __forceinline__ void collide(const Landau<A>& lw, A T, A inv_tau, Get&& get, Put&& put) {
-  const EqCoef<L::ORDER, A> c = eq_coef<L::ORDER, A>(lw.n, T, lw.U0);
+  const LevCoef<L, A> e = level_coef<L, A>(eq_coef<L::ORDER, A>(lw.n, T, lw.U0));
   const A a = lw.U0 * inv_tau;
   static_for<L::NDP>([&](auto K) {
     constexpr int k = decltype(K)::value;
@@ -397,42 +434,23 @@ __device__ __forceinline__ void collide(const Landau<A>& lw, A T, A inv_tau, Get
     constexpr int np = L::DP_NPAIR[k];
     constexpr int vx = L::VX[first], vy = L::VY[first], vz = L::VZ[first];
     constexpr double ir = L::INV_R;
-    A t = A(0);
+    A t = A(0);  // direction +v: t; mirror -v: -t
     if constexpr (vx != 0) t = fma(A(vx * ir), lw.Ux, t);
     if constexpr (vy != 0) t = fma(A(vy * ir), lw.Uy, t);
     if constexpr (vz != 0) t = fma(A(vz * ir), lw.Uz, t);
-    // direction +v: t; mirror -v: -t
-    const A q1o = c.c01 * t;
-    const A q1p = c.c10 + q1o, q1m = c.c10 - q1o;
-    const A up = fma(c.T, t, c.x), um = fma(-c.T, t, c.x);
-    // qNp / qNm: coefficient of p0^N for direction +v / -v
-    A q2p, q2m, q3p, q3m;
-    if constexpr (L::ORDER == 3) {
-      const A q2e = fma(c.c02, t * t, c.c20), q2o = c.c11 * t;
-      q2p = q2e + q2o;
-      q2m = q2e - q2o;
-      q3p = c.pref * (up * up * up);
-      q3m = c.pref * (um * um * um);
-    } else {
-      q2p = c.pref * (up * up);
-      q2m = c.pref * (um * um);
-      q3p = q3m = A(0);
-    }
     const A omp = fma(-t, inv_tau, a), omm = fma(t, inv_tau, a);
     static_for<np>([&](auto J) {
       constexpr int ip = first + 2 * decltype(J)::value;
-      constexpr double p0d = L::P0[L::LEV[ip]];
+      constexpr int l = L::LEV[ip];
       constexpr double wd = L::W[ip];
-      const A p0 = A(p0d), w = A(wd);
+      const A w = A(wd);
       A Ep, Em;
       if constexpr (L::ORDER == 3) {
-        Ep = fma(p0, fma(p0, fma(p0, q3p, q2p), q1p), c.c00);
-        Em = fma(p0, fma(p0, fma(p0, q3m, q2m), q1m), c.c00);
+        Ep = fma(t, fma(t, fma(t, e.d[l], e.c[l]), e.b[l]), e.a[l]);
+        Em = fma(-t, fma(-t, fma(-t, e.d[l], e.c[l]), e.b[l]), e.a[l]);
       } else {
-        Ep = fma(p0, fma(p0, q2p, q1p), c.c00);
-        Em = fma(p0, fma(p0, q2m, q1m), c.c00);
-        (void)q3p;
-        (void)q3m;
+        Ep = fma(t, fma(t, e.c[l], e.b[l]), e.a[l]);
+        Em = fma(-t, fma(-t, e.c[l], e.b[l]), e.a[l]);
       }
       const A fp = get(ic<ip>{}), fm = get(ic<ip + 1>{});
       put(ic<ip>{}, fma(omp, fma(w, Ep, -fp), fp));
@@ -525,11 +543,8 @@ __device__ __forceinline__ Mom<float> moments_f2(Get2&& get2) {
 
 template <class L, class Get2, class Put2>
 __device__ __forceinline__ void collide_f2(const Landau<float>& lw, float T, float inv_tau, Get2&& get2, Put2&& put2) {
-  const EqCoef<L::ORDER, float> c = eq_coef<L::ORDER, float>(lw.n, T, lw.U0);
+  const LevCoef<L, float> e = level_coef<L, float>(eq_coef<L::ORDER, float>(lw.n, T, lw.U0));
   const float a = lw.U0 * inv_tau;
-  const float2 Tp = f2(c.T, c.T), xp = f2(c.x, c.x), prefp = f2(c.pref, c.pref);
-  const float2 c00p = f2(c.c00, c.c00), c10p = f2(c.c10, c.c10), c01p = f2(c.c01, c.c01);
-  const float2 c20p = f2(c.c20, c.c20), c11p = f2(c.c11, c.c11), c02p = f2(c.c02, c.c02);
   const float2 Uxp = f2(lw.Ux, lw.Ux), Uyp = f2(lw.Uy, lw.Uy), Uzp = f2(lw.Uz, lw.Uz);
   const float2 itp = f2(inv_tau, inv_tau), nap = f2(-a, -a);
   static_for<L::NDP>([&](auto K) {
@@ -542,28 +557,17 @@ __device__ __forceinline__ void collide_f2(const Landau<float>& lw, float T, flo
     if constexpr (vx != 0) tt = ffma2(f2((float)(vx * ir), (float)(-vx * ir)), Uxp, tt);
     if constexpr (vy != 0) tt = ffma2(f2((float)(vy * ir), (float)(-vy * ir)), Uyp, tt);
     if constexpr (vz != 0) tt = ffma2(f2((float)(vz * ir), (float)(-vz * ir)), Uzp, tt);
-    const float2 up = ffma2(Tp, tt, xp);    // x + T t
-    const float2 q1 = ffma2(c01p, tt, c10p);
-    float2 q2, q3;
-    if constexpr (L::ORDER == 3) {
-      const float2 e2 = ffma2(c02p, fmul2(tt, tt), c20p);
-      q2 = ffma2(c11p, tt, e2);
-      q3 = fmul2(prefp, fmul2(fmul2(up, up), up));
-    } else {
-      q2 = fmul2(prefp, fmul2(up, up));
-      q3 = f2(0.f, 0.f);
-    }
     const float2 nom = ffma2(itp, tt, nap);  // -(U0 - t) / tau' for +v, -(U0 + t) / tau' for -v
     static_for<np>([&](auto J) {
       constexpr int ip = first + 2 * decltype(J)::value;
-      constexpr float p0 = (float)L::P0[L::LEV[ip]];
+      constexpr int l = L::LEV[ip];
       constexpr float nw = (float)(-L::W[ip]);
-      const float2 p0p = f2(p0, p0);
       float2 E;
       if constexpr (L::ORDER == 3)
-        E = ffma2(p0p, ffma2(p0p, ffma2(p0p, q3, q2), q1), c00p);
+        E = ffma2(tt, ffma2(tt, ffma2(tt, f2(e.d[l], e.d[l]), f2(e.c[l], e.c[l])), f2(e.b[l], e.b[l])),
+                  f2(e.a[l], e.a[l]));
       else
-        E = ffma2(p0p, ffma2(p0p, q2, q1), c00p);
+        E = ffma2(tt, ffma2(tt, f2(e.c[l], e.c[l]), f2(e.b[l], e.b[l])), f2(e.a[l], e.a[l]));
       const float2 f = get2(ic<ip>{});
       const float2 d = ffma2(f2(nw, nw), E, f);  // f - w E
       put2(ic<ip>{}, ffma2(nom, d, f));        // f - omega (f - w E)
