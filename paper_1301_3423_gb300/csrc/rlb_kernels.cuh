@@ -84,6 +84,11 @@ struct StoreF16Dev {
     constexpr float iw = (float)(1.0 / L::W[I]);
     *p = __float2half_rn(fmaf(v, iw, -sp.half_nref));
   }
+  // the deviation d_i itself (the step kernels work in deviation space)
+  template <class L, int I>
+  __device__ static __forceinline__ A load_dev(const T* p, const StepParams&) { return __half2float(__ldg(p)); }
+  template <class L, int I>
+  __device__ static __forceinline__ void store_dev(T* p, A d, const StepParams&) { *p = __float2half_rn(d); }
   template <class L, int I>
   __device__ static __forceinline__ double to_f64(T v, const StepParams& sp) {
     constexpr double w = L::W[I];
@@ -179,8 +184,41 @@ struct Mom {
   A N0, Nx, Ny, Nz, T00, T0x, T0y, T0z, Txx, Tyy, Tzz, Txy, Txz, Tyz;
 };
 
-template <class L, class A, class Get>
-__device__ __forceinline__ Mom<A> moments(Get&& get) {
+// Moments of the weights alone, sum_i w_i k_i for the moment kernels k_i of N^0, T^00 and T^ab:
+// in deviation space (f_i = w_i (d_i + c)) the constant c contributes c times these.  The odd
+// moments cancel exactly between mirror partners.
+template <class L>
+struct RestSums {
+  static constexpr double sum(int e, int a, int b) {  // sum_i w_i p0^e (v_a v_b / R^2 if a >= 0)
+    double s = 0.0;
+    for (int i = 0; i < L::Q; ++i) {
+      const double p = L::P0[L::LEV[i]];
+      const double v[3] = {(double)L::VX[i], (double)L::VY[i], (double)L::VZ[i]};
+      double t = L::W[i] * (e == 1 ? p : p * p);
+      if (a >= 0) t *= v[a] * v[b] * L::INV_R2;
+      s += t;
+    }
+    return s;
+  }
+  static constexpr double N0 = sum(1, -1, -1), T00 = sum(2, -1, -1), Txx = sum(2, 0, 0), Tyy = sum(2, 1, 1),
+                          Txy = sum(2, 0, 1), Txz = sum(2, 0, 2), Tyz = sum(2, 1, 2);
+};
+
+template <class L, class A>
+__device__ __forceinline__ void add_rest_sums(Mom<A>& m, A c) {
+  m.N0 = fma(A(RestSums<L>::N0), c, m.N0);
+  m.T00 = fma(A(RestSums<L>::T00), c, m.T00);
+  m.Txx = fma(A(RestSums<L>::Txx), c, m.Txx);
+  m.Tyy = fma(A(RestSums<L>::Tyy), c, m.Tyy);
+  m.Txy = fma(A(RestSums<L>::Txy), c, m.Txy);
+  m.Txz = fma(A(RestSums<L>::Txz), c, m.Txz);
+  m.Tyz = fma(A(RestSums<L>::Tyz), c, m.Tyz);
+}
+
+// DEV = true: get returns deviations d_i = f_i / w_i - c, and the moments are those of
+// f_i = w_i (d_i + c).
+template <class L, class A, bool DEV = false, class Get>
+__device__ __forceinline__ Mom<A> moments(Get&& get, A c = A(0)) {
   Mom<A> m;
   m.N0 = m.Nx = m.Ny = m.Nz = A(0);
   m.T00 = m.T0x = m.T0y = m.T0z = A(0);
@@ -192,14 +230,15 @@ __device__ __forceinline__ Mom<A> moments(Get&& get) {
     A s1p = A(0), s1m = A(0), s2p = A(0), s2m = A(0);
     static_for<np>([&](auto J) {
       constexpr int ip = first + 2 * decltype(J)::value;
+      constexpr double wk = DEV ? L::W[ip] : 1.0;  // mirror partners share the weight
       constexpr double p0 = L::P0[L::LEV[ip]];
       const A fa = get(ic<ip>{});
       const A fb = get(ic<ip + 1>{});
       const A sp = fa + fb, sm = fa - fb;
-      s1p = fma(A(p0), sp, s1p);
-      s1m = fma(A(p0), sm, s1m);
-      s2p = fma(A(p0 * p0), sp, s2p);
-      s2m = fma(A(p0 * p0), sm, s2m);
+      s1p = fma(A(wk * p0), sp, s1p);
+      s1m = fma(A(wk * p0), sm, s1m);
+      s2p = fma(A(wk * p0 * p0), sp, s2p);
+      s2m = fma(A(wk * p0 * p0), sm, s2m);
     });
     constexpr int vx = L::VX[first], vy = L::VY[first], vz = L::VZ[first];
     constexpr double ir = L::INV_R, ir2 = L::INV_R2;
@@ -223,6 +262,7 @@ __device__ __forceinline__ Mom<A> moments(Get&& get) {
     if constexpr (vx != 0 && vz != 0) m.Txz = fma(A(vx * vz * ir2), s2p, m.Txz);
     if constexpr (vy != 0 && vz != 0) m.Tyz = fma(A(vy * vz * ir2), s2p, m.Tyz);
   });
+  if constexpr (DEV) add_rest_sums<L, A>(m, c);
   // |v|^2 = R^2 for every velocity, so the spatial trace of T equals T^00.
   m.Tzz = m.T00 - m.Txx - m.Tyy;
   return m;
@@ -397,8 +437,9 @@ struct LevCoef {
   A a[L::NLEV], b[L::NLEV], c[L::NLEV], d[L::NLEV];
 };
 
+// shift: subtracted from every a_l (deviation space evaluates E - c)
 template <class L, class A>
-__device__ __forceinline__ LevCoef<L, A> level_coef(const EqCoef<L::ORDER, A>& q) {
+__device__ __forceinline__ LevCoef<L, A> level_coef(const EqCoef<L::ORDER, A>& q, A shift = A(0)) {
   LevCoef<L, A> r;
   static_for<L::NLEV>([&](auto K) {
     constexpr int l = decltype(K)::value;
@@ -410,13 +451,13 @@ __device__ __forceinline__ LevCoef<L, A> level_coef(const EqCoef<L::ORDER, A>& q
       r.d[l] = pp3 * (q.T * q.T * q.T);
       r.c[l] = fma(A(3) * ppx, q.T * q.T, p2 * q.c02);
       r.b[l] = fma(A(3) * ppx * q.x, q.T, fma(p2, q.c11, p * q.c01));
-      r.a[l] = fma(ppx * q.x, q.x, fma(p2, q.c20, fma(p, q.c10, q.c00)));
+      r.a[l] = fma(ppx * q.x, q.x, fma(p2, q.c20, fma(p, q.c10, q.c00 - shift)));
     } else {
       const A pp2 = p2 * q.pref;  // pref p0^2
       r.d[l] = A(0);
       r.c[l] = pp2 * (q.T * q.T);
       r.b[l] = fma(A(2) * pp2 * q.x, q.T, p * q.c01);
-      r.a[l] = fma(pp2 * q.x, q.x, fma(p, q.c10, q.c00));
+      r.a[l] = fma(pp2 * q.x, q.x, fma(p, q.c10, q.c00 - shift));
     }
   });
   return r;
@@ -424,9 +465,11 @@ __device__ __forceinline__ LevCoef<L, A> level_coef(const EqCoef<L::ORDER, A>& q
 
 // Collision of one cell (Eq. (rlb:disc) right-hand side, delta t' = 1):
 //   f*_i = f_i + omega_i (w_i E_i - f_i),  omega_i = p_i.U / (tau' p0_i) = (U0 - t_i) / tau'.
-template <class L, class A, class Get, class Put>
-__device__ __forceinline__ void collide(const Landau<A>& lw, A T, A inv_tau, Get&& get, Put&& put) {
-  const LevCoef<L, A> e = level_coef<L, A>(eq_coef<L::ORDER, A>(lw.n, T, lw.U0));
+// DEV = true: get / put carry deviations d_i = f_i / w_i - c, and the collision is
+// d_i + omega_i ((E_i - c) - d_i).
+template <class L, class A, bool DEV = false, class Get, class Put>
+__device__ __forceinline__ void collide(const Landau<A>& lw, A T, A inv_tau, Get&& get, Put&& put, A c = A(0)) {
+  const LevCoef<L, A> e = level_coef<L, A>(eq_coef<L::ORDER, A>(lw.n, T, lw.U0), DEV ? c : A(0));
   const A a = lw.U0 * inv_tau;
   static_for<L::NDP>([&](auto K) {
     constexpr int k = decltype(K)::value;
@@ -453,8 +496,14 @@ __device__ __forceinline__ void collide(const Landau<A>& lw, A T, A inv_tau, Get
         Em = fma(-t, fma(-t, e.c[l], e.b[l]), e.a[l]);
       }
       const A fp = get(ic<ip>{}), fm = get(ic<ip + 1>{});
-      put(ic<ip>{}, fma(omp, fma(w, Ep, -fp), fp));
-      put(ic<ip + 1>{}, fma(omm, fma(w, Em, -fm), fm));
+      if constexpr (DEV) {
+        put(ic<ip>{}, fma(omp, Ep - fp, fp));
+        put(ic<ip + 1>{}, fma(omm, Em - fm, fm));
+        (void)w;
+      } else {
+        put(ic<ip>{}, fma(omp, fma(w, Ep, -fp), fp));
+        put(ic<ip + 1>{}, fma(omm, fma(w, Em, -fm), fm));
+      }
     });
   });
 }
@@ -470,8 +519,8 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return _
 __device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
-template <class L, class Get2>
-__device__ __forceinline__ Mom<float> moments_f2(Get2&& get2) {
+template <class L, bool DEV = false, class Get2>
+__device__ __forceinline__ Mom<float> moments_f2(Get2&& get2, float c = 0.f) {
   const float2 z = f2(0.f, 0.f);
   float2 N0 = z, Nx = z, Ny = z, Nz = z, T00 = z, T0x = z, T0y = z, T0z = z, Txx = z, Tyy = z, Txy = z, Txz = z, Tyz = z;
   static_for<L::NDP>([&](auto K) {
@@ -481,8 +530,9 @@ __device__ __forceinline__ Mom<float> moments_f2(Get2&& get2) {
     float2 S1 = z, S2 = z;  // (sum over energies for +v, for -v)
     static_for<np>([&](auto J) {
       constexpr int ip = first + 2 * decltype(J)::value;
-      constexpr float p0 = (float)L::P0[L::LEV[ip]];
-      constexpr float p02 = (float)(L::P0[L::LEV[ip]] * L::P0[L::LEV[ip]]);
+      constexpr double wk = DEV ? L::W[ip] : 1.0;  // mirror partners share the weight
+      constexpr float p0 = (float)(wk * L::P0[L::LEV[ip]]);
+      constexpr float p02 = (float)(wk * L::P0[L::LEV[ip]] * L::P0[L::LEV[ip]]);
       const float2 f = get2(ic<ip>{});
       S1 = ffma2(f2(p0, p0), f, S1);
       S2 = ffma2(f2(p02, p02), f, S2);
@@ -537,13 +587,15 @@ __device__ __forceinline__ Mom<float> moments_f2(Get2&& get2) {
   m.Txy = Txy.x + Txy.y;
   m.Txz = Txz.x + Txz.y;
   m.Tyz = Tyz.x + Tyz.y;
+  if constexpr (DEV) add_rest_sums<L, float>(m, c);
   m.Tzz = m.T00 - m.Txx - m.Tyy;
   return m;
 }
 
-template <class L, class Get2, class Put2>
-__device__ __forceinline__ void collide_f2(const Landau<float>& lw, float T, float inv_tau, Get2&& get2, Put2&& put2) {
-  const LevCoef<L, float> e = level_coef<L, float>(eq_coef<L::ORDER, float>(lw.n, T, lw.U0));
+template <class L, bool DEV = false, class Get2, class Put2>
+__device__ __forceinline__ void collide_f2(const Landau<float>& lw, float T, float inv_tau, Get2&& get2, Put2&& put2,
+                                           float c = 0.f) {
+  const LevCoef<L, float> e = level_coef<L, float>(eq_coef<L::ORDER, float>(lw.n, T, lw.U0), DEV ? c : 0.f);
   const float a = lw.U0 * inv_tau;
   const float2 Uxp = f2(lw.Ux, lw.Ux), Uyp = f2(lw.Uy, lw.Uy), Uzp = f2(lw.Uz, lw.Uz);
   const float2 itp = f2(inv_tau, inv_tau), nap = f2(-a, -a);
@@ -561,7 +613,7 @@ __device__ __forceinline__ void collide_f2(const Landau<float>& lw, float T, flo
     static_for<np>([&](auto J) {
       constexpr int ip = first + 2 * decltype(J)::value;
       constexpr int l = L::LEV[ip];
-      constexpr float nw = (float)(-L::W[ip]);
+      constexpr float nw = DEV ? -1.f : (float)(-L::W[ip]);
       float2 E;
       if constexpr (L::ORDER == 3)
         E = ffma2(tt, ffma2(tt, ffma2(tt, f2(e.d[l], e.d[l]), f2(e.c[l], e.c[l])), f2(e.b[l], e.b[l])),
@@ -569,7 +621,7 @@ __device__ __forceinline__ void collide_f2(const Landau<float>& lw, float T, flo
       else
         E = ffma2(tt, ffma2(tt, f2(e.c[l], e.c[l]), f2(e.b[l], e.b[l])), f2(e.a[l], e.a[l]));
       const float2 f = get2(ic<ip>{});
-      const float2 d = ffma2(f2(nw, nw), E, f);  // f - w E
+      const float2 d = ffma2(f2(nw, nw), E, f);  // f - w E (deviation space: d - (E - c))
       put2(ic<ip>{}, ffma2(nom, d, f));        // f - omega (f - w E)
     });
   });
@@ -583,7 +635,9 @@ __device__ __forceinline__ void collide_f2(const Landau<float>& lw, float T, flo
 //   bit 0: scalar arithmetic (0) or mirror pairs in float2 with paired FMA (1);
 //   bit 1: registers as needed, 2 resident blocks of 128 threads per SM (0), or at most 168
 //          registers for 3 resident blocks (1; the compiler spills a little).
-// (Also measured slower and not built: staging part of the populations in shared memory; a
+// (Also measured slower and not built: keeping half-deviation populations as packed half2 pairs
+// at 4 resident blocks (128 registers still spill); staging part of the populations in shared
+// memory; a
 // persistent interior kernel that prefetches each thread's next cell into shared memory with
 // cp.async while it computes the current one; and two passes over the populations, moments then
 // collision, at 64-80 registers and 6-8 resident blocks with L2 evict-last / evict-first hints,
@@ -619,22 +673,34 @@ __device__ __forceinline__ void step_cell(const typename S::T* __restrict__ src,
   const bool fast = PATH == kPathRow && row_fast;
   const ST* __restrict__ base = src + cl.c;
   ST* __restrict__ out = dst + cl.c;
+  // Half-deviation storage works in deviation space: the values in flight are d_i = f_i / w_i - c
+  // as stored, and the moments and collision take the weights and c into their constants.
+  constexpr bool DEV = std::is_same<S, StoreF16Dev>::value;
+  const A c_dev = DEV ? A(p.half_nref) : A(0);
+  auto ld = [&](auto I, const ST* ptr) -> A {
+    constexpr int i = decltype(I)::value;
+    if constexpr (DEV) return S::template load_dev<L, i>(ptr, p);
+    else return S::template load<L, i>(ptr, p);
+  };
 
   auto load = [&](auto I) -> A {
     constexpr int i = decltype(I)::value;
-    if (fast) return S::template load<L, i>(base + p.off[i], p);
-    if constexpr (PATH == kPathRow) return S::template load<L, i>(base + x_row_offset<L, i, WALLS>(cl, p), p);
-    else return S::template load<L, i>(src + pull_index<L, i, GENERAL, WALLS>(cl, p), p);
+    if (fast) return ld(I, base + p.off[i]);
+    if constexpr (PATH == kPathRow) return ld(I, base + x_row_offset<L, i, WALLS>(cl, p));
+    else return ld(I, src + pull_index<L, i, GENERAL, WALLS>(cl, p));
   };
   auto store = [&](auto I, A v) {
     constexpr int i = decltype(I)::value;
-    if (valid) S::template store<L, i>(out + (long long)i * p.cells, v, p);
+    if (valid) {
+      if constexpr (DEV) S::template store_dev<L, i>(out + (long long)i * p.cells, v, p);
+      else S::template store<L, i>(out + (long long)i * p.cells, v, p);
+    }
   };
 
   A fk[KEEP ? L::Q : 1];
   if constexpr (KEEP) {
     // one warp-uniform branch around the whole pull, so the fast path is plain constant offsets
-    if (fast) static_for<L::Q>([&](auto I) { fk[decltype(I)::value] = S::template load<L, decltype(I)::value>(base + p.off[decltype(I)::value], p); });
+    if (fast) static_for<L::Q>([&](auto I) { fk[decltype(I)::value] = ld(I, base + p.off[decltype(I)::value]); });
     else static_for<L::Q>([&](auto I) { fk[decltype(I)::value] = load(I); });
   }
   auto get = [&](auto I) -> A {
@@ -647,8 +713,8 @@ __device__ __forceinline__ void step_cell(const typename S::T* __restrict__ src,
   };
 
   Mom<A> m;
-  if constexpr (PACKED) m = moments_f2<L>(get2);
-  else m = moments<L, A>(get);
+  if constexpr (PACKED) m = moments_f2<L, DEV>(get2, (float)c_dev);
+  else m = moments<L, A, DEV>(get, c_dev);
   const Landau<A> lw = landau_step<A>(m, p);
   if (!lw.ok) {
     // no Landau frame: record it and stream the populations without collision
@@ -666,9 +732,9 @@ __device__ __forceinline__ void step_cell(const typename S::T* __restrict__ src,
       store(ic<i>{}, v.x);
       store(ic<i + 1>{}, v.y);
     };
-    collide_f2<L>(lw, T, inv_tau, get2, put2);
+    collide_f2<L, DEV>(lw, T, inv_tau, get2, put2, (float)c_dev);
   } else {
-    collide<L, A>(lw, T, inv_tau, get, store);
+    collide<L, A, DEV>(lw, T, inv_tau, get, store, c_dev);
   }
 }
 
