@@ -637,12 +637,11 @@ __device__ __forceinline__ void collide_f2(const Landau<float>& lw, float T, flo
 //          registers for 3 resident blocks (1; the compiler spills a little).
 // (Also measured slower and not built: keeping half-deviation populations as packed half2 pairs
 // at 4 resident blocks (128 registers still spill); staging part of the populations in shared
-// memory; a
-// persistent interior kernel that prefetches each thread's next cell into shared memory with
-// cp.async while it computes the current one; and two passes over the populations, moments then
-// collision, at 64-80 registers and 6-8 resident blocks with L2 evict-last / evict-first hints,
-// whose second pass executed about 50% more instructions and still missed L2 on a third of its
-// reads.)
+// memory; a persistent interior kernel that prefetches each thread's next cell into shared memory
+// with cp.async while it computes the current one; and two passes over the populations, moments
+// then collision, at 64-80 registers and 6-8 resident blocks with L2 evict-last / evict-first
+// hints, whose second pass executed about 50% more instructions and still missed L2 on a third
+// of its reads.)
 // Double arithmetic pulls each population twice (moments, then collision) and has one variant.
 enum StepVariant : int { kRegScalar = 0, kRegPacked = 1, kReg3Scalar = 2, kReg3Packed = 3, kNumVariants = 4 };
 
