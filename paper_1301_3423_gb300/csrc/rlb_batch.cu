@@ -36,6 +36,8 @@ struct rlb_batch {
   std::vector<Member> members;   // slot -> member (ctx == nullptr: free slot)
   BatchMember* d_members = nullptr;
   int d_capacity = 0;
+  int* d_tile_member = nullptr;  // member index of every tile of the uploaded table
+  int tm_capacity = 0;
   int* d_counters = nullptr;     // one tile counter per launch of a run
   long counters_capacity = 0;
   const Launchers* launch = nullptr;
@@ -122,6 +124,7 @@ extern "C" long rlb_batch_steps_left(const rlb_batch* b, int slot) {
 // Member table of a run: the active members in slot order with their tile ranges.
 static rlb_status upload_table(rlb_batch* b, long nsteps, int* nmembers, int* total_tiles) {
   std::vector<BatchMember> t;
+  std::vector<int> tm;
   int tiles = 0;
   b->walls = 0;
   for (const Member& m : b->members) {
@@ -137,6 +140,7 @@ static rlb_status upload_table(rlb_batch* b, long nsteps, int* nmembers, int* to
     if (d.p.has_wall) b->walls = 1;
     d.int_tiles = (d.p.int_warps + kStepThreads / 32 - 1) / (kStepThreads / 32);
     tiles += d.int_tiles + (d.p.shell_cells + kStepThreads - 1) / kStepThreads;
+    tm.resize(tiles, (int)t.size());
     t.push_back(d);
   }
   *nmembers = (int)t.size();
@@ -154,7 +158,21 @@ static rlb_status upload_table(rlb_batch* b, long nsteps, int* nmembers, int* to
     b->d_capacity = cap;
     ++b->version;  // a captured graph holds the old table pointer
   }
+  if (tiles > b->tm_capacity) {
+    if (b->d_tile_member) cudaFree(b->d_tile_member);
+    b->d_tile_member = nullptr;
+    const int cap = std::max<int>(tiles, 2 * b->tm_capacity);
+    cudaError_t e = cudaMalloc((void**)&b->d_tile_member, (size_t)cap * sizeof(int));
+    if (e != cudaSuccess) {
+      b->tm_capacity = 0;
+      return bfail(b, RLB_ENOMEM, std::string("tile table: ") + cudaGetErrorString(e));
+    }
+    b->tm_capacity = cap;
+    ++b->version;  // a captured graph holds the old table pointer
+  }
   BATCH_CUDA(b, cudaMemcpyAsync(b->d_members, t.data(), t.size() * sizeof(BatchMember), cudaMemcpyHostToDevice,
+                                b->stream));
+  BATCH_CUDA(b, cudaMemcpyAsync(b->d_tile_member, tm.data(), tm.size() * sizeof(int), cudaMemcpyHostToDevice,
                                 b->stream));
   BATCH_CUDA(b, cudaStreamSynchronize(b->stream));  // the host vector goes away
   return RLB_OK;
@@ -182,7 +200,8 @@ static rlb_status enqueue_run(rlb_batch* b, long nsteps, int nmem, int tiles, in
   const int grid = grid_of(b, variant);
   for (long k = 0; k < nsteps; ++k) {
     cudaError_t e =
-        b->launch->batch_step(b->d_members, nmem, tiles, (int)k, b->d_counters, variant, b->walls, grid, b->stream);
+        b->launch->batch_step(b->d_members, b->d_tile_member, tiles, (int)k, b->d_counters, variant, b->walls, grid,
+                              b->stream);
     ++b->launches;
     if (e != cudaSuccess) return bfail(b, RLB_ECUDA, std::string("batched step: ") + cudaGetErrorString(e));
   }
@@ -288,7 +307,8 @@ extern "C" rlb_status rlb_batch_autotune(rlb_batch* b, int reps, int* variant, d
         if (r == 1) BATCH_CUDA(b, cudaEventRecord(e0, b->stream));
         // every repetition is launch 0 of the same run: the same next state into the spare buffers
         cudaError_t e =
-            b->launch->batch_step(b->d_members, nmem, tiles, 0, b->d_counters + r, v, b->walls, grid, b->stream);
+            b->launch->batch_step(b->d_members, b->d_tile_member, tiles, 0, b->d_counters + r, v, b->walls, grid,
+                                  b->stream);
         if (e != cudaSuccess) return bfail(b, RLB_ECUDA, std::string("batched step: ") + cudaGetErrorString(e));
       }
       BATCH_CUDA(b, cudaEventRecord(e1, b->stream));
@@ -328,6 +348,7 @@ extern "C" rlb_status rlb_batch_destroy(rlb_batch* b) {
   cudaStreamSynchronize(b->stream);
   if (b->graph.exec) cudaGraphExecDestroy(b->graph.exec);
   if (b->d_members) cudaFree(b->d_members);
+  if (b->d_tile_member) cudaFree(b->d_tile_member);
   if (b->d_counters) cudaFree(b->d_counters);
   delete b;
   return RLB_OK;

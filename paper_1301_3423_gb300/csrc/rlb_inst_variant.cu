@@ -36,10 +36,10 @@ cudaError_t RLB_VFN(step, RLB_INST_VARIANT)(const void* src, void* dst, const St
   return cudaGetLastError();
 }
 
-cudaError_t RLB_VFN(batch, RLB_INST_VARIANT)(const BatchMember* m, int n, int tiles, int li, int* counters, int walls,
-                                             int grid, cudaStream_t s) {
-  if (walls) k_step_batch<L, S, V, true><<<grid, kStepThreads, 0, s>>>(m, n, tiles, li, counters);
-  else k_step_batch<L, S, V, false><<<grid, kStepThreads, 0, s>>>(m, n, tiles, li, counters);
+cudaError_t RLB_VFN(batch, RLB_INST_VARIANT)(const BatchMember* m, const int* tm, int tiles, int li, int* counters,
+                                             int walls, int grid, cudaStream_t s) {
+  if (walls) k_step_batch<L, S, V, true><<<grid, kStepThreads, 0, s>>>(m, tm, tiles, li, counters);
+  else k_step_batch<L, S, V, false><<<grid, kStepThreads, 0, s>>>(m, tm, tiles, li, counters);
   return cudaGetLastError();
 }
 

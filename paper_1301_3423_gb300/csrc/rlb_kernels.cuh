@@ -801,8 +801,9 @@ __global__ void __launch_bounds__(kStepThreads, StepShape<S, VARIANT>::kMinBlock
 
 // ---------------------------------------------------------------------------------------------
 // Batched step: many independent lattices (members) advance together.  A persistent grid takes
-// tiles from one shared queue (an atomic counter per launch); a tile belongs to one member, found
-// by binary search over the members' first tile.  A member's tiles are first its row tiles, four
+// tiles from one shared queue (an atomic counter per launch); a tile's member comes from a tile ->
+// member table, and a block copies a member's parameters to shared memory only when its member
+// changes.  A member's tiles are first its row tiles, four
 // warps of the row kernel's segments each (constant offsets, or x wrapped only), then its shell
 // tiles of kStepThreads shell cells (every coordinate wrapped): the decomposition of a solo step,
 // so a member's populations are bitwise those of the same steps taken alone with the same variant.
@@ -811,33 +812,30 @@ __global__ void __launch_bounds__(kStepThreads, StepShape<S, VARIANT>::kMinBlock
 
 template <class L, class S, int VARIANT, bool WALLS>
 __global__ void __launch_bounds__(kStepThreads, StepShape<S, VARIANT>::kMinBlocks)
-    k_step_batch(const BatchMember* __restrict__ members, int nmembers, int total_tiles, int launch_index,
-                 int* __restrict__ counters) {
+    k_step_batch(const BatchMember* __restrict__ members, const int* __restrict__ tile_member, int total_tiles,
+                 int launch_index, int* __restrict__ counters) {
   using ST = typename S::T;
   __shared__ StepParams sp;
   __shared__ int s_tile, s_member;
+  int held = -1;  // member whose parameters sp holds (block-uniform)
   for (;;) {
     if (threadIdx.x == 0) {
       const int t = atomicAdd(&counters[launch_index], 1);
-      int lo = 0, hi = nmembers - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (members[mid].tile_begin <= t) lo = mid;
-        else hi = mid - 1;
-      }
       s_tile = t;
-      s_member = lo;
+      s_member = t < total_tiles ? __ldg(&tile_member[t]) : 0;
     }
     __syncthreads();
     const int tile = s_tile;
+    const int mi = s_member;
     if (tile >= total_tiles) return;
-    const BatchMember& m = members[s_member];
+    const BatchMember& m = members[mi];
     const bool active = launch_index < m.steps_left;
-    if (active) {
-      // the member's parameters into shared memory (one copy per tile instead of global reads)
+    if (active && mi != held) {
+      // the member's parameters into shared memory, once per change of member
       const int* srcw = reinterpret_cast<const int*>(&m.p);
       int* dstw = reinterpret_cast<int*>(&sp);
       for (int k = threadIdx.x; k < (int)(sizeof(StepParams) / sizeof(int)); k += kStepThreads) dstw[k] = srcw[k];
+      held = mi;
     }
     __syncthreads();
     if (active) {

@@ -18,7 +18,7 @@ struct Launchers {
   int step_variants;  // number of step-kernel variants the autotuner may choose from
   // one launch of the persistent batched step (grid blocks over the shared tile queue); walls != 0
   // selects the kernel with the bounce-back test (some member has walls)
-  cudaError_t (*batch_step)(const BatchMember* members, int nmembers, int total_tiles, int launch_index,
+  cudaError_t (*batch_step)(const BatchMember* members, const int* tile_member, int total_tiles, int launch_index,
                             int* counters, int variant, int walls, int grid, cudaStream_t s);
   // resident blocks per SM of the batched step for a variant
   int (*batch_blocks_per_sm)(int variant);
