@@ -82,7 +82,9 @@ typedef struct {
   double dx_fm;       /* cell size in fm (default 0.008, Sec. III) */
   double T_unit_GeV;  /* lattice temperature unit in GeV (default 0.4, Sec. III) */
   int storage;        /* rlb_storage */
-  int landau_fp64;    /* RLB_F32 / RLB_F16DEV only: 1 = always solve Landau matching in double */
+  int landau_fp64;    /* RLB_F32 / RLB_F16DEV only: 1 = solve Landau matching in double for every
+                         cell (from the Eckart vector to 1e-12 U0); 0 = in float, in double for
+                         cells above gamma_thr */
   double gamma_thr;   /* RLB_F32 / RLB_F16DEV only: cells whose Eckart Lorentz factor exceeds this
                          are solved in double (default 2.0) */
   double n_ref;       /* RLB_F16DEV only: reference density of the stored deviation (default 1.0) */
@@ -162,8 +164,9 @@ rlb_status rlb_autotune(rlb_ctx* ctx, int reps, int* variant, double ms[RLB_MAX_
 /* ---------------------------------------------------------------------------------------------
  * Batched stepping.  A batch steps many contexts of the same order and storage together: each
  * launch of a persistent kernel advances every member with steps left by one time step of
- * Eq. (rlb:disc), taking tiles of 128 cells from one queue shared by all members, so lattices of
- * very different sizes fill the GPU together.  Members keep their own buffers, parameters, status
+ * Eq. (rlb:disc), taking tiles from one queue shared by all members (a member's tiles are its
+ * interior rows in 32-cell segments, four per tile, then its boundary cells, 128 per tile), so
+ * lattices of very different sizes fill the GPU together.  Members keep their own buffers, parameters, status
  * and step counters; a member's populations after a batched run are bitwise those of the same
  * steps taken alone with the same step-kernel variant.  Members must use the batch's stream.
  * ------------------------------------------------------------------------------------------- */
