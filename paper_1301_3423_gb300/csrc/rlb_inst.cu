@@ -47,10 +47,13 @@ int batch_blocks_per_sm(int variant) {
 cudaError_t fields(const void* src, const StepParams& p, double* f, double* partial, int* status, bool pull,
                    cudaStream_t s) {
   const int blocks = (p.cells + kMomThreads - 1) / kMomThreads;
-  if (pull)
-    k_fields<L, S, true><<<blocks, kMomThreads, 0, s>>>((const T*)src, p, f, partial, status);
+  // the modulo wrap only for lattices with a periodic axis shorter than the stencil reach
+  if (pull && p.general)
+    k_fields<L, S, true, true><<<blocks, kMomThreads, 0, s>>>((const T*)src, p, f, partial, status);
+  else if (pull)
+    k_fields<L, S, true, false><<<blocks, kMomThreads, 0, s>>>((const T*)src, p, f, partial, status);
   else
-    k_fields<L, S, false><<<blocks, kMomThreads, 0, s>>>((const T*)src, p, f, partial, status);
+    k_fields<L, S, false, false><<<blocks, kMomThreads, 0, s>>>((const T*)src, p, f, partial, status);
   return cudaGetLastError();
 }
 

@@ -864,13 +864,15 @@ __global__ void __launch_bounds__(kStepThreads, StepShape<S, VARIANT>::kMinBlock
 }
 
 // ---------------------------------------------------------------------------------------------
-// fields and conserved densities of one time level (double arithmetic)
-//   PULL = true : the pre-collision populations pulled from the previous state
+// fields and conserved densities of one time level (double arithmetic; for float storages the
+// Landau solve starts from the float solution and stops at 1e-12 U0)
+//   PULL = true : the pre-collision populations pulled from the previous state (GENERAL: modulo
+//                 wrap, for periodic axes shorter than the stencil reach)
 //   PULL = false: the stored populations of each cell
 // fields[k][cell], k = n, eps, U0, U1, U2, U3; partial[block][5] = block sums of
 // N^0, T^00, T^0x, T^0y, T^0z, reduced by warp shuffles in a fixed order.
 // ---------------------------------------------------------------------------------------------
-template <class L, class S, bool PULL>
+template <class L, class S, bool PULL, bool GENERAL>
 __global__ void __launch_bounds__(kMomThreads) k_fields(const typename S::T* __restrict__ src,
                                                         const __grid_constant__ StepParams p,
                                                         double* __restrict__ fields,
@@ -881,11 +883,19 @@ __global__ void __launch_bounds__(kMomThreads) k_fields(const typename S::T* __r
   const Cell cl = make_cell(valid ? gid : p.cells - 1, p);
   auto get = [&](auto I) -> double {
     constexpr int i = decltype(I)::value;
-    const long long idx = PULL ? pull_index<L, i, true, true>(cl, p) : (long long)i * p.cells + cl.c;
+    const long long idx = PULL ? pull_index<L, i, GENERAL, true>(cl, p) : (long long)i * p.cells + cl.c;
     return S::template to_f64<L, i>(src[idx], p);
   };
   const Mom<double> m = moments<L, double>(get);
-  const Landau<double> lw = landau<double, 200>(m);
+  Landau<double> lw;
+  if constexpr (std::is_same<typename S::A, double>::value) {
+    lw = landau<double, 200>(m);
+  } else {
+    // float populations: start from the float solution, stop at 1e-12 U0 (float carries no more)
+    const Landau<float> lf = landau<float, 8>(convert<double, float>(m));
+    if (lf.ok) lw = landau_from<double, 200>(m, (double)lf.U0, (double)lf.Ux, (double)lf.Uy, (double)lf.Uz, 1e-12);
+    else lw = landau<double, 200>(m);
+  }
   if (valid) {
     const double nan = __longlong_as_double(0x7ff8000000000000ll);
     fields[0 * (long long)p.cells + cl.c] = lw.ok ? lw.n : nan;
@@ -917,7 +927,8 @@ __global__ void __launch_bounds__(kMomThreads) k_fields(const typename S::T* __r
 }
 
 // ---------------------------------------------------------------------------------------------
-// initial state f_i = f_i^eq(n, T, u) (double arithmetic), and population format conversion
+// initial state f_i = f_i^eq(n, T, u) (double arithmetic, per-level form), and population format
+// conversion
 // ---------------------------------------------------------------------------------------------
 template <class L, class S>
 __global__ void __launch_bounds__(128) k_init(const double* __restrict__ n, const double* __restrict__ Tf,
@@ -935,7 +946,8 @@ __global__ void __launch_bounds__(128) k_init(const double* __restrict__ n, cons
   }
   const double g = rsqrt(1.0 - u2);
   const double Ux = g * ux, Uy = g * uy, Uz = g * uz;
-  const EqCoef<L::ORDER, double> cf = eq_coef<L::ORDER, double>(nn, T, g);
+  // the equilibrium per energy level (see level_coef), in double
+  const LevCoef<L, double> e = level_coef<L, double>(eq_coef<L::ORDER, double>(nn, T, g));
   static_for<L::NDP>([&](auto K) {
     constexpr int k = decltype(K)::value;
     constexpr int first = L::DP_FIRST[k];
@@ -944,22 +956,12 @@ __global__ void __launch_bounds__(128) k_init(const double* __restrict__ n, cons
     const double t = (vx * Ux + vy * Uy + vz * Uz) * L::INV_R;
     static_for<np>([&](auto J) {
       constexpr int ip = first + 2 * decltype(J)::value;
-      constexpr double p0 = L::P0[L::LEV[ip]];
+      constexpr int l = L::LEV[ip];
       constexpr double w = L::W[ip];
-      for (int sgn = 0; sgn < 2; ++sgn) {
-        const double tt = sgn ? -t : t;
-        const double u_ = fma(cf.T, tt, cf.x);
-        double E;
-        if constexpr (L::ORDER == 3)
-          E = cf.c00 + p0 * (cf.c10 + cf.c01 * tt + p0 * (cf.c20 + cf.c11 * tt + cf.c02 * tt * tt +
-                                                          p0 * cf.pref * u_ * u_ * u_));
-        else
-          E = cf.c00 + p0 * (cf.c10 + cf.c01 * tt + p0 * cf.pref * u_ * u_);
-        if (sgn == 0)
-          S::template store<L, ip>(dst + (long long)ip * cells + c, (typename S::A)(w * E), p);
-        else
-          S::template store<L, ip + 1>(dst + (long long)(ip + 1) * cells + c, (typename S::A)(w * E), p);
-      }
+      const double Ep = fma(t, fma(t, fma(t, e.d[l], e.c[l]), e.b[l]), e.a[l]);
+      const double Em = fma(-t, fma(-t, fma(-t, e.d[l], e.c[l]), e.b[l]), e.a[l]);
+      S::template store<L, ip>(dst + (long long)ip * cells + c, (typename S::A)(w * Ep), p);
+      S::template store<L, ip + 1>(dst + (long long)(ip + 1) * cells + c, (typename S::A)(w * Em), p);
     });
   });
 }
