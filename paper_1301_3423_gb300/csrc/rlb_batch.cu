@@ -25,7 +25,7 @@ struct Member {
 struct GraphCache {
   cudaGraphExec_t exec = nullptr;
   long nsteps = 0, version = -1;
-  int variant = -1, nmembers = 0, tiles = 0, walls = -1;
+  int variant = -1, nmembers = 0, tiles = 0, row_tiles = -1, walls = -1;
 };
 
 }  // namespace
@@ -38,11 +38,12 @@ struct rlb_batch {
   int d_capacity = 0;
   int* d_tile_member = nullptr;  // member index of every tile of the uploaded table
   int tm_capacity = 0;
-  int* d_counters = nullptr;     // one tile counter per launch of a run
+  int* d_counters = nullptr;     // two tile counters (row queue, shell queue) per step of a run
   long counters_capacity = 0;
   const Launchers* launch = nullptr;
   int variant = 0;
   int walls = 0;                 // some member of the uploaded table has bounce-back walls
+  int row_tiles = 0, shell_tiles = 0;  // of the uploaded table: row tiles first, then shell tiles
   int sms = 0;
   long version = 0;              // bumps when the member set changes
   long launches = 0;
@@ -124,8 +125,7 @@ extern "C" long rlb_batch_steps_left(const rlb_batch* b, int slot) {
 // Member table of a run: the active members in slot order with their tile ranges.
 static rlb_status upload_table(rlb_batch* b, long nsteps, int* nmembers, int* total_tiles) {
   std::vector<BatchMember> t;
-  std::vector<int> tm;
-  int tiles = 0;
+  std::vector<int> row_tm, shell_tm;
   b->walls = 0;
   for (const Member& m : b->members) {
     if (!m.ctx || m.steps_left <= 0) continue;
@@ -136,13 +136,20 @@ static rlb_status upload_table(rlb_batch* b, long nsteps, int* nmembers, int* to
     d.status = m.ctx->status;
     d.parity0 = m.ctx->cur;
     d.steps_left = (int)std::min<long>(m.steps_left, nsteps);
-    d.tile_begin = tiles;
     if (d.p.has_wall) b->walls = 1;
-    d.int_tiles = (d.p.int_warps + kStepThreads / 32 - 1) / (kStepThreads / 32);
-    tiles += d.int_tiles + (d.p.shell_cells + kStepThreads - 1) / kStepThreads;
-    tm.resize(tiles, (int)t.size());
+    // row tiles: 4 row-kernel warps; shell tiles: kStepThreads shell cells
+    d.row_tile_begin = (int)row_tm.size();
+    row_tm.resize(row_tm.size() + (d.p.int_warps + kStepThreads / 32 - 1) / (kStepThreads / 32), (int)t.size());
+    d.shell_tile_begin = (int)shell_tm.size();  // shifted by the row tiles below
+    shell_tm.resize(shell_tm.size() + (d.p.shell_cells + kStepThreads - 1) / kStepThreads, (int)t.size());
     t.push_back(d);
   }
+  b->row_tiles = (int)row_tm.size();
+  b->shell_tiles = (int)shell_tm.size();
+  for (BatchMember& d : t) d.shell_tile_begin += b->row_tiles;
+  std::vector<int> tm(row_tm);
+  tm.insert(tm.end(), shell_tm.begin(), shell_tm.end());
+  const int tiles = (int)tm.size();
   *nmembers = (int)t.size();
   *total_tiles = tiles;
   if (t.empty()) return RLB_OK;
@@ -196,13 +203,15 @@ static int grid_of(rlb_batch* b, int variant) { return b->sms * b->launch->batch
 
 // Enqueue nsteps launches (launch index 0..nsteps-1) directly on the stream.
 static rlb_status enqueue_run(rlb_batch* b, long nsteps, int nmem, int tiles, int variant) {
-  BATCH_CUDA(b, cudaMemsetAsync(b->d_counters, 0, (size_t)nsteps * sizeof(int), b->stream));
+  (void)nmem;
+  (void)tiles;
+  BATCH_CUDA(b, cudaMemsetAsync(b->d_counters, 0, (size_t)(2 * nsteps) * sizeof(int), b->stream));
   const int grid = grid_of(b, variant);
   for (long k = 0; k < nsteps; ++k) {
     cudaError_t e =
-        b->launch->batch_step(b->d_members, b->d_tile_member, tiles, (int)k, b->d_counters, variant, b->walls, grid,
-                              b->stream);
-    ++b->launches;
+        b->launch->batch_step(b->d_members, b->d_tile_member, b->row_tiles, b->shell_tiles, (int)k, b->d_counters,
+                              variant, b->walls, grid, b->stream);
+    b->launches += (b->row_tiles > 0) + (b->shell_tiles > 0);
     if (e != cudaSuccess) return bfail(b, RLB_ECUDA, std::string("batched step: ") + cudaGetErrorString(e));
   }
   return RLB_OK;
@@ -216,7 +225,7 @@ extern "C" rlb_status rlb_batch_run(rlb_batch* b, long nsteps, int use_graph, in
       return bfail(b, RLB_EINVAL, "rlb_batch_run: a member uses another stream than the batch");
   int nmem = 0, tiles = 0;
   if (nsteps > 0) {
-    rlb_status st = ensure_counters(b, nsteps);
+    rlb_status st = ensure_counters(b, 2 * nsteps);
     if (st != RLB_OK) return st;
     st = upload_table(b, nsteps, &nmem, &tiles);
     if (st != RLB_OK) return st;
@@ -225,10 +234,10 @@ extern "C" rlb_status rlb_batch_run(rlb_batch* b, long nsteps, int use_graph, in
     if (use_graph) {
       // the table lives at a fixed device address and is refreshed before every replay, so the
       // captured launches stay valid while nsteps, the variant, the member set and the active
-      // members' tile count stay the same
+      // members' row and shell tile counts stay the same
       GraphCache& gc = b->graph;
       if (!gc.exec || gc.nsteps != nsteps || gc.version != b->version || gc.variant != b->variant ||
-          gc.nmembers != nmem || gc.tiles != tiles || gc.walls != b->walls) {
+          gc.nmembers != nmem || gc.tiles != tiles || gc.row_tiles != b->row_tiles || gc.walls != b->walls) {
         if (b->graph.exec) cudaGraphExecDestroy(b->graph.exec);
         b->graph.exec = nullptr;
         cudaStream_t cs;
@@ -256,10 +265,11 @@ extern "C" rlb_status rlb_batch_run(rlb_batch* b, long nsteps, int use_graph, in
         gc.variant = b->variant;
         gc.nmembers = nmem;
         gc.tiles = tiles;
+        gc.row_tiles = b->row_tiles;
         gc.walls = b->walls;
       }
       BATCH_CUDA(b, cudaGraphLaunch(b->graph.exec, b->stream));
-      b->launches += nsteps;
+      b->launches += nsteps * ((b->row_tiles > 0) + (b->shell_tiles > 0));
     } else {
       rlb_status st = enqueue_run(b, nsteps, nmem, tiles, b->variant);
       if (st != RLB_OK) return st;
@@ -289,7 +299,7 @@ extern "C" rlb_status rlb_batch_autotune(rlb_batch* b, int reps, int* variant, d
     if (m.ctx && m.ctx->have_prev)
       return bfail(b, RLB_ESTATE, "rlb_batch_autotune: only while no member has taken a step");
   int nmem = 0, tiles = 0;
-  rlb_status st = ensure_counters(b, reps + 1);
+  rlb_status st = ensure_counters(b, 2 * (reps + 1));
   if (st != RLB_OK) return st;
   st = upload_table(b, 1, &nmem, &tiles);  // steps_left = 1: every launch redoes launch 0
   if (st != RLB_OK) return st;
@@ -302,13 +312,13 @@ extern "C" rlb_status rlb_batch_autotune(rlb_batch* b, int reps, int* variant, d
     int choice = b->variant;
     for (int v = 0; v < b->launch->step_variants; ++v) {
       const int grid = grid_of(b, v);
-      BATCH_CUDA(b, cudaMemsetAsync(b->d_counters, 0, (size_t)(reps + 1) * sizeof(int), b->stream));
+      BATCH_CUDA(b, cudaMemsetAsync(b->d_counters, 0, (size_t)(2 * (reps + 1)) * sizeof(int), b->stream));
       for (int r = 0; r <= reps; ++r) {
         if (r == 1) BATCH_CUDA(b, cudaEventRecord(e0, b->stream));
         // every repetition is launch 0 of the same run: the same next state into the spare buffers
         cudaError_t e =
-            b->launch->batch_step(b->d_members, b->d_tile_member, tiles, 0, b->d_counters + r, v, b->walls, grid,
-                                  b->stream);
+            b->launch->batch_step(b->d_members, b->d_tile_member, b->row_tiles, b->shell_tiles, 0,
+                                  b->d_counters + 2 * r, v, b->walls, grid, b->stream);
         if (e != cudaSuccess) return bfail(b, RLB_ECUDA, std::string("batched step: ") + cudaGetErrorString(e));
       }
       BATCH_CUDA(b, cudaEventRecord(e1, b->stream));

@@ -46,9 +46,8 @@ struct BatchMember {
   int* status;        // the member's status words
   int parity0;        // buffer holding the state before launch 0 of this run
   int steps_left;     // launches with index >= steps_left leave this member alone
-  int tile_begin;     // first tile of this member in the queue
-  int int_tiles;      // its first int_tiles tiles are row tiles (4 row-kernel warps), the rest shell
-                      // tiles (kStepThreads shell cells)
+  int row_tile_begin;    // first of its row tiles (4 row-kernel warps each) in the row queue
+  int shell_tile_begin;  // first of its shell tiles (kStepThreads shell cells each) in the shell queue
 };
 
 }  // namespace rlb

@@ -19,17 +19,17 @@ cudaError_t step(const void* src, void* dst, const StepParams& p, int* status, b
   return RLB_VFN(step, 0)(src, dst, p, status, general, s);
 }
 
-cudaError_t batch_step(const BatchMember* m, const int* tm, int tiles, int li, int* counters, int variant, int walls,
-                       int grid, cudaStream_t s) {
+cudaError_t batch_step(const BatchMember* m, const int* tm, int row_tiles, int shell_tiles, int li, int* counters,
+                       int variant, int walls, int grid, cudaStream_t s) {
   if (kFloat) {
     switch (variant < kVariants ? variant : 0) {
-      case 1: return RLB_VFN(batch, 1)(m, tm, tiles, li, counters, walls, grid, s);
-      case 2: return RLB_VFN(batch, 2)(m, tm, tiles, li, counters, walls, grid, s);
-      case 3: return RLB_VFN(batch, 3)(m, tm, tiles, li, counters, walls, grid, s);
+      case 1: return RLB_VFN(batch, 1)(m, tm, row_tiles, shell_tiles, li, counters, walls, grid, s);
+      case 2: return RLB_VFN(batch, 2)(m, tm, row_tiles, shell_tiles, li, counters, walls, grid, s);
+      case 3: return RLB_VFN(batch, 3)(m, tm, row_tiles, shell_tiles, li, counters, walls, grid, s);
       default: break;
     }
   }
-  return RLB_VFN(batch, 0)(m, tm, tiles, li, counters, walls, grid, s);
+  return RLB_VFN(batch, 0)(m, tm, row_tiles, shell_tiles, li, counters, walls, grid, s);
 }
 
 int batch_blocks_per_sm(int variant) {

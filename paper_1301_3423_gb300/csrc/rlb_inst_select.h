@@ -39,8 +39,8 @@ constexpr int kVariants = kFloat ? kNumVariants : 1;
 #define RLB_DECLARE_VARIANT(v)                                                                               \
   cudaError_t RLB_VFN(step, v)(const void* src, void* dst, const StepParams& p, int* status, bool general,   \
                                cudaStream_t s);                                                              \
-  cudaError_t RLB_VFN(batch, v)(const BatchMember* m, const int* tm, int tiles, int li, int* counters,      \
-                                int walls, int grid, cudaStream_t s);                                                             \
+  cudaError_t RLB_VFN(batch, v)(const BatchMember* m, const int* tm, int row_tiles, int shell_tiles, int li, \
+                                int* counters, int walls, int grid, cudaStream_t s);                                                             \
   int RLB_VFN(occupancy, v)();
 RLB_DECLARE_VARIANT(0)
 RLB_DECLARE_VARIANT(1)

@@ -36,16 +36,28 @@ cudaError_t RLB_VFN(step, RLB_INST_VARIANT)(const void* src, void* dst, const St
   return cudaGetLastError();
 }
 
-cudaError_t RLB_VFN(batch, RLB_INST_VARIANT)(const BatchMember* m, const int* tm, int tiles, int li, int* counters,
-                                             int walls, int grid, cudaStream_t s) {
-  if (walls) k_step_batch<L, S, V, true><<<grid, kStepThreads, 0, s>>>(m, tm, tiles, li, counters);
-  else k_step_batch<L, S, V, false><<<grid, kStepThreads, 0, s>>>(m, tm, tiles, li, counters);
+namespace {
+template <bool W>
+void launch_batch(const BatchMember* m, const int* tm, int row_tiles, int shell_tiles, int li, int* counters, int grid,
+                  cudaStream_t s) {
+  if (row_tiles > 0)
+    k_step_batch<L, S, V, W, true><<<grid, kStepThreads, 0, s>>>(m, tm, 0, row_tiles, li, counters + 2 * li);
+  if (shell_tiles > 0)
+    k_step_batch<L, S, V, W, false>
+        <<<grid, kStepThreads, 0, s>>>(m, tm, row_tiles, row_tiles + shell_tiles, li, counters + 2 * li + 1);
+}
+}  // namespace
+
+cudaError_t RLB_VFN(batch, RLB_INST_VARIANT)(const BatchMember* m, const int* tm, int row_tiles, int shell_tiles,
+                                             int li, int* counters, int walls, int grid, cudaStream_t s) {
+  if (walls) launch_batch<true>(m, tm, row_tiles, shell_tiles, li, counters, grid, s);
+  else launch_batch<false>(m, tm, row_tiles, shell_tiles, li, counters, grid, s);
   return cudaGetLastError();
 }
 
 int RLB_VFN(occupancy, RLB_INST_VARIANT)() {
   int nb = 0;  // both instantiations have the same launch bounds
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_batch<L, S, V, false>, kStepThreads, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_batch<L, S, V, false, true>, kStepThreads, 0) !=
       cudaSuccess) {
     cudaGetLastError();
     return 1;

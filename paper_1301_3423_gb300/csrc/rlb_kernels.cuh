@@ -800,38 +800,37 @@ __global__ void __launch_bounds__(kStepThreads, StepShape<S, VARIANT>::kMinBlock
 }
 
 // ---------------------------------------------------------------------------------------------
-// Batched step: many independent lattices (members) advance together.  A persistent grid takes
-// tiles from one shared queue (an atomic counter per launch); a tile's member comes from a tile ->
-// member table, and a block copies a member's parameters to shared memory only when its member
-// changes.  A member's tiles are first its row tiles, four
-// warps of the row kernel's segments each (constant offsets, or x wrapped only), then its shell
-// tiles of kStepThreads shell cells (every coordinate wrapped): the decomposition of a solo step,
-// so a member's populations are bitwise those of the same steps taken alone with the same variant.
-// Each launch is one time step of every member whose step count is not yet reached.
+// Batched step: many independent lattices (members) advance together.  Each time step is two
+// persistent launches, one over the members' row tiles (four row-kernel warps each: constant
+// offsets, or x wrapped only) and one over their shell tiles (kStepThreads shell cells each, every
+// coordinate wrapped): the decomposition of a solo step, so a member's populations are bitwise those
+// of the same steps taken alone with the same variant, and each kernel carries one pull path.
+// Blocks take tiles from the launch's queue (an atomic counter); a tile's member comes from a
+// tile -> member table (row tiles first, then shell tiles), and a block copies a member's
+// parameters to shared memory only when its member changes.  Members whose step count is reached
+// are skipped.
 // ---------------------------------------------------------------------------------------------
-
-template <class L, class S, int VARIANT, bool WALLS>
+template <class L, class S, int VARIANT, bool WALLS, bool ROWS>
 __global__ void __launch_bounds__(kStepThreads, StepShape<S, VARIANT>::kMinBlocks)
-    k_step_batch(const BatchMember* __restrict__ members, const int* __restrict__ tile_member, int total_tiles,
-                 int launch_index, int* __restrict__ counters) {
+    k_step_batch(const BatchMember* __restrict__ members, const int* __restrict__ tile_member, int tile_begin,
+                 int tile_end, int launch_index, int* __restrict__ counter) {
   using ST = typename S::T;
   __shared__ StepParams sp;
   __shared__ int s_tile, s_member;
   int held = -1;  // member whose parameters sp holds (block-uniform)
   for (;;) {
     if (threadIdx.x == 0) {
-      const int t = atomicAdd(&counters[launch_index], 1);
+      const int t = tile_begin + atomicAdd(counter, 1);
       s_tile = t;
-      s_member = t < total_tiles ? __ldg(&tile_member[t]) : 0;
+      s_member = t < tile_end ? __ldg(&tile_member[t]) : 0;
     }
     __syncthreads();
     const int tile = s_tile;
     const int mi = s_member;
-    if (tile >= total_tiles) return;
+    if (tile >= tile_end) return;
     const BatchMember& m = members[mi];
     const bool active = launch_index < m.steps_left;
     if (active && mi != held) {
-      // the member's parameters into shared memory, once per change of member
       const int* srcw = reinterpret_cast<const int*>(&m.p);
       int* dstw = reinterpret_cast<int*>(&sp);
       for (int k = threadIdx.x; k < (int)(sizeof(StepParams) / sizeof(int)); k += kStepThreads) dstw[k] = srcw[k];
@@ -840,11 +839,10 @@ __global__ void __launch_bounds__(kStepThreads, StepShape<S, VARIANT>::kMinBlock
     __syncthreads();
     if (active) {
       const int par = (m.parity0 + launch_index) & 1;
-      const int lt = tile - m.tile_begin;
       const ST* sb = static_cast<const ST*>(m.buf[par]);
       ST* db = static_cast<ST*>(m.buf[par ^ 1]);
-      if (lt < m.int_tiles) {
-        const int w = lt * (kStepThreads / 32) + (threadIdx.x >> 5);
+      if constexpr (ROWS) {
+        const int w = (tile - m.row_tile_begin) * (kStepThreads / 32) + (threadIdx.x >> 5);
         if (w < sp.int_warps) {  // whole warps only
           Cell cl;
           bool valid, fast;
@@ -852,7 +850,7 @@ __global__ void __launch_bounds__(kStepThreads, StepShape<S, VARIANT>::kMinBlock
           step_cell<L, S, false, VARIANT, kPathRow, WALLS>(sb, db, sp, m.status, cl, valid, fast);
         }
       } else {
-        const int s = (lt - m.int_tiles) * kStepThreads + threadIdx.x;
+        const int s = (tile - m.shell_tile_begin) * kStepThreads + threadIdx.x;
         const bool valid = s < sp.shell_cells;
         const Cell cl = shell_cell(valid ? s : sp.shell_cells - 1, sp);
         if (sp.general) step_cell<L, S, true, VARIANT, kPathEdge, WALLS>(sb, db, sp, m.status, cl, valid);

@@ -16,10 +16,12 @@ struct Launchers {
                       cudaStream_t s);
   cudaError_t (*convert)(void* pop, double* dbl, int i0, int i1, bool to_f64, const StepParams& p, cudaStream_t s);
   int step_variants;  // number of step-kernel variants the autotuner may choose from
-  // one launch of the persistent batched step (grid blocks over the shared tile queue); walls != 0
-  // selects the kernel with the bounce-back test (some member has walls)
-  cudaError_t (*batch_step)(const BatchMember* members, const int* tile_member, int total_tiles, int launch_index,
-                            int* counters, int variant, int walls, int grid, cudaStream_t s);
+  // one time step of the persistent batched kernels: a launch over the row tiles [0, row_tiles) and
+  // one over the shell tiles [row_tiles, row_tiles + shell_tiles) of the tile -> member table, with
+  // counters[2 launch_index] and counters[2 launch_index + 1]; walls != 0 selects the kernels with
+  // the bounce-back test (some member has walls)
+  cudaError_t (*batch_step)(const BatchMember* members, const int* tile_member, int row_tiles, int shell_tiles,
+                            int launch_index, int* counters, int variant, int walls, int grid, cudaStream_t s);
   // resident blocks per SM of the batched step for a variant
   int (*batch_blocks_per_sm)(int variant);
 };
