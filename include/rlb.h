@@ -163,10 +163,10 @@ rlb_status rlb_autotune(rlb_ctx* ctx, int reps, int* variant, double ms[RLB_MAX_
 
 /* ---------------------------------------------------------------------------------------------
  * Batched stepping.  A batch steps many contexts of the same order and storage together: each
- * launch of a persistent kernel advances every member with steps left by one time step of
- * Eq. (rlb:disc), taking tiles from one queue shared by all members (a member's tiles are its
- * interior rows in 32-cell segments, four per tile, then its boundary cells, 128 per tile), so
- * lattices of very different sizes fill the GPU together.  Members keep their own buffers, parameters, status
+ * time step of Eq. (rlb:disc) is two launches of persistent kernels that advance every member
+ * with steps left, taking tiles from queues shared by all members (first the members' interior
+ * rows in 32-cell segments, four per tile, then their boundary cells, 128 per tile), so lattices of
+ * very different sizes fill the GPU together.  Members keep their own buffers, parameters, status
  * and step counters; a member's populations after a batched run are bitwise those of the same
  * steps taken alone with the same step-kernel variant.  Members must use the batch's stream.
  * ------------------------------------------------------------------------------------------- */
