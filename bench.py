@@ -139,14 +139,47 @@ def recorded_traffic(n_side, variant, density):
     return rec.get("dram_bytes_per_step")
 
 
-def dist_setup():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+def dist_env():
+    """(world, rank, local rank) from the torchrun environment (1, 0, 0 without it)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def dist_setup(backend=None):
+    """One process per GPU: join the process group when world > 1 (NCCL when CUDA is present,
+    else gloo, or `backend`).  The replicas exchange only timings, never simulation data."""
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
-    return world, rank, local
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    """The maximum of x over all ranks (the slowest replica's time)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, cells, steps, ms_max):
+    """Whole-job cell updates per second (MLUPS) of `world` replicas that each took `steps` steps
+    of `cells` cells, over the slowest replica's time."""
+    return world * cells * steps / (ms_max * 1e-3) / 1e6
 
 
 def cpu_baseline(n, T, u, budget_s=12.0, planes=2):
@@ -302,7 +335,8 @@ def run_reference(args, world, rank):
         return
     N = args.n
     n, T, u = gen.smooth_random_fields((N, N, N), seed=1, vmax=0.6, sigma_lnT=args.sigma, density=args.density)
-    cb = cpu_baseline(n, T, u, budget_s=max(10.0, min(60.0, 0.1 * args.steps)))
+    budget = args.cpu_budget if args.cpu_budget > 0 else max(10.0, min(60.0, 0.1 * args.steps))
+    cb = cpu_baseline(n, T, u, budget_s=budget)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -319,7 +353,7 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--n", type=int, default=N_LATTICE, help="lattice edge (default 256)")
+    ap.add_argument("--n", "--lattice", dest="n", type=int, default=N_LATTICE, help="lattice edge (default 256)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -332,11 +366,15 @@ def main():
     ap.add_argument("--density", default=DENSITY, choices=["uniform", "cube"],
                     help="initial density: uniform n = 1, or n = T^3")
     ap.add_argument("--sigma", type=float, default=SIGMA_LNT, help="std of ln T")
+    ap.add_argument("--cpu-budget", type=float, default=0.0,
+                    help="seconds of oracle work for the CPU baseline / reference arm (0: default)")
     args = ap.parse_args()
-    world, rank, local = dist_setup()
     if args.impl == "reference":
+        # rank 0 alone times the oracle; the other ranks exit without work (no process group)
+        world, rank, _ = dist_env()
         run_reference(args, world, rank)
         return
+    world, rank, local = dist_setup()
 
     import torch
 
@@ -349,18 +387,6 @@ def main():
     cells = N ** 3
     n, T, u = gen.smooth_random_fields(shape, seed=1 + rank, vmax=0.6, sigma_lnT=args.sigma, density=args.density)
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
 
     # ---- device-resident throughput (the headline value) ------------------------------------
     g = RLB(shape, order=ORDER, storage="f32", eta_over_s=ETA_S, stream=stream, step_variant=args.variant)
@@ -373,7 +399,7 @@ def main():
     g.sync()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = g.kernel_launches
-    barrier()
+    barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(torch.cuda.current_device()) as clk:
         t_wall = time.perf_counter()
@@ -383,12 +409,12 @@ def main():
         e1.synchronize()
         t_wall = time.perf_counter() - t_wall
     torch.cuda.synchronize()
-    barrier()
+    barrier(world)
     launches = g.kernel_launches - launches0
     ms_total = e0.elapsed_time(e1)
-    ms_total_max = max_over_ranks(ms_total)
+    ms_total_max = max_over_ranks(ms_total, world)
     g.sync()  # raises if any cell lost its Landau frame: a broken simulation is not a measurement
-    value = world * cells * args.steps / (ms_total_max * 1e-3) / 1e6
+    value = job_value(world, cells, args.steps, ms_total_max)
     # A step is one launch of the interior kernel plus one of the shell kernel (disjoint cells):
     # the roofline takes the algorithmic bytes of the whole step over the step's device time.
     per_step_s = ms_total * 1e-3 / args.steps
@@ -410,7 +436,7 @@ def main():
         g64.step(k64)
         e1.record(stream)
         e1.synchronize()
-        ms64 = max_over_ranks(e0.elapsed_time(e1))
+        ms64 = max_over_ranks(e0.elapsed_time(e1), world)
         g64.sync()
         g64.close()
         fp64 = {"value": world * cells * k64 / (ms64 * 1e-3) / 1e6, "unit": "MLUPS", "steps": k64,
@@ -444,13 +470,13 @@ def main():
         ge.init(ptr(hn), ptr(hT), ptr(hu))
         ge.step(args.warmup)
         ge.sync()
-        barrier()
+        barrier(world)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ge.init(ptr(hn), ptr(hT), ptr(hu))
         ge.step(args.steps)
         ge.moments(out=dict(n=on.numpy(), eps=oe.numpy(), U=oU.numpy()))
-        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        t_e2e = max_over_ranks(time.perf_counter() - t0, world)
         ge.close()
         h2d = 5 * cells * 8
         d2h = 6 * cells * 8 + 5 * 8
