@@ -225,6 +225,9 @@ extern "C" rlb_status rlb_create(const rlb_params* p, rlb_ctx** out) {
   sp.int_segs = in[0] > 0 ? (p->nx + 31) / 32 : 0;
   sp.int_warps = sp.int_segs * in[1] * in[2];
   sp.shell_cells = c->cells - (in[0] > 0 ? p->nx * in[1] * in[2] : 0);
+  sp.row_segs = (p->nx + 31) / 32;
+  sp.shell_rows = sp.shell_cells / p->nx;  // the shell is made of whole rows
+  sp.shell_warps = sp.shell_rows * sp.row_segs;
 
   const size_t pop_bytes = (size_t)c->q * c->cells * c->elem;
   c->fblocks = (c->cells + kMomThreads - 1) / kMomThreads;

@@ -32,6 +32,9 @@ struct StepParams {
   int int_segs;             // 32-aligned warp segments per row of the row kernel (all nx cells)
   int int_warps;            // interior segments in total
   int shell_cells;          // cells outside the interior box
+  int row_segs;             // 32-aligned warp segments per row (all nx cells)
+  int shell_rows;           // rows whose y or z lies outside the interior box
+  int shell_warps;          // shell_rows * row_segs
 };
 
 // per-axis boundary codes, as in rlb_bc

@@ -18,11 +18,12 @@ void launch_step(const void* src, void* dst, const StepParams& p, int* status, b
     k_step_interior<L, S, V, W><<<blocks, kStepThreads, 0, s>>>((const T*)src, (T*)dst, p, status);
   }
   if (p.shell_cells > 0) {
-    const int blocks = (p.shell_cells + kStepThreads - 1) / kStepThreads;
-    if (general)
+    if (general) {
+      const int blocks = (p.shell_cells + kStepThreads - 1) / kStepThreads;
       k_step_shell<L, S, true, V, W><<<blocks, kStepThreads, 0, s>>>((const T*)src, (T*)dst, p, status);
-    else
-      k_step_shell<L, S, false, V, W><<<blocks, kStepThreads, 0, s>>>((const T*)src, (T*)dst, p, status);
+    } else {
+      k_step_shell_rows<L, S, V, W><<<p.shell_warps, 32, 0, s>>>((const T*)src, (T*)dst, p, status);
+    }
   }
 }
 }  // namespace

@@ -425,6 +425,24 @@ __device__ __forceinline__ EqCoef<ORDER, A> eq_coef(A n, A T, A U0) {
   return c;
 }
 
+// Pull offset of population I from the cell's own index in a shell row: the constant offset plus
+// the y and z wrap (or clamp) shifts of the row, plus the x shift unless the warp's x segment is
+// interior; the cell's own reversed population beyond a bounce-back wall.
+template <class L, int I, bool WALLS>
+__device__ __forceinline__ long long shell_row_offset(const Cell& cl, const StepParams& p, const bool xfast) {
+  constexpr int vx = L::VX[I], vy = L::VY[I], vz = L::VZ[I];
+  if constexpr (WALLS) {
+    if (p.has_wall && beyond_wall<L, I>(cl, p)) return (long long)(I ^ 1) * p.cells;
+  }
+  long long o = p.off[I];
+  if constexpr (vy != 0) o += (long long)(src_coord<vy, false>(cl.y, p.ny, p.bc[1]) - (cl.y - vy)) * p.nx;
+  if constexpr (vz != 0) o += (long long)(src_coord<vz, false>(cl.z, p.nz, p.bc[2]) - (cl.z - vz)) * p.nxy;
+  if constexpr (vx != 0) {
+    if (!xfast) o += src_coord<vx, false>(cl.x, p.nx, p.bc[0]) - (cl.x - vx);
+  }
+  return o;
+}
+
 // The equilibrium as a polynomial in t per energy level l (p0 = p0_l):
 //   E(p0_l, t) = a_l + t (b_l + t (c_l + t d_l)),
 //   order 3: a = c00 + p0 c10 + p0^2 c20 + pref p0^3 x^3,  b = p0 c01 + p0^2 c11 + 3 pref p0^3 x^2 T,
@@ -652,9 +670,11 @@ struct StepShape {
 };
 
 // How a step kernel pulls: the row kernel's warps lie in rows with interior y and z and are told
-// whether their x segment is interior too (constant offsets) or not (only x wraps); the shell
-// kernel wraps every coordinate.
-enum PullPath : int { kPathRow = 1, kPathEdge = 2 };
+// whether their x segment is interior too (constant offsets) or not (only x wraps); the shell row
+// kernel's warps lie in boundary rows, whose y and z shifts are the same for the whole warp; the
+// per-cell shell kernel (lattices shorter than the stencil reach) wraps every coordinate of every
+// cell.
+enum PullPath : int { kPathRow = 1, kPathEdge = 2, kPathShellRow = 3 };
 
 // One cell's time step (pull, moments, Landau matching, equilibrium, collision, store).  Invalid
 // lanes (valid = false) carry a clamped in-range cell, compute and store nothing.
@@ -668,7 +688,7 @@ __device__ __forceinline__ void step_cell(const typename S::T* __restrict__ src,
   constexpr bool KEEP = StepShape<S, VARIANT>::kKeep;
   // Warp-uniform choice: a row warp whose segment is interior pulls with constant offsets; other
   // row warps wrap x only; shell cells resolve wrap / copy-out / bounce-back per population.
-  static_assert(PATH == kPathRow || PATH == kPathEdge, "pull path");
+  static_assert(PATH == kPathRow || PATH == kPathEdge || PATH == kPathShellRow, "pull path");
   const bool fast = PATH == kPathRow && row_fast;
   const ST* __restrict__ base = src + cl.c;
   ST* __restrict__ out = dst + cl.c;
@@ -686,6 +706,7 @@ __device__ __forceinline__ void step_cell(const typename S::T* __restrict__ src,
     constexpr int i = decltype(I)::value;
     if (fast) return ld(I, base + p.off[i]);
     if constexpr (PATH == kPathRow) return ld(I, base + x_row_offset<L, i, WALLS>(cl, p));
+    else if constexpr (PATH == kPathShellRow) return ld(I, base + shell_row_offset<L, i, WALLS>(cl, p, row_fast));
     else return ld(I, src + pull_index<L, i, GENERAL, WALLS>(cl, p));
   };
   auto store = [&](auto I, A v) {
@@ -764,6 +785,46 @@ __global__ void __launch_bounds__(kStepThreads, StepShape<S, VARIANT>::kMinBlock
   bool valid, fast;
   row_cell(w, threadIdx.x & 31, p, cl, valid, fast);
   step_cell<L, S, false, VARIANT, kPathRow, WALLS>(src, dst, p, status, cl, valid, fast);
+}
+
+// Row r of the shell: the rows of the z-boundary planes, then the y-boundary rows of the interior
+// planes.
+__device__ __forceinline__ void shell_row(int r, const StepParams& p, int& y, int& z) {
+  const int A = (p.nz - p.izn) * p.ny;
+  if (r < A) {
+    const int zz = r / p.ny;
+    y = r - zz * p.ny;
+    z = zz < p.iz0 ? zz : zz + p.izn;
+  } else {
+    r -= A;
+    const int wy = p.ny - p.iyn;
+    const int zz = r / wy, yy = r - zz * wy;
+    z = p.iz0 + zz;
+    y = yy < p.iy0 ? yy : yy + p.iyn;
+  }
+}
+
+// Shell rows for lattices whose periodic axes are all at least the stencil reach: warp w covers
+// the 32-aligned x segment w % row_segs of shell row w / row_segs, so the y and z shifts of each
+// population are the same for the whole warp and x wraps only in segments outside the interior x
+// range.
+// One warp per block, so that the row (and with it every population's y and z shift) derives from
+// blockIdx alone, a value the compiler knows to be the same for the whole warp; as many blocks
+// per SM as the four-warp kernels have warps.
+template <class L, class S, int VARIANT, bool WALLS>
+__global__ void __launch_bounds__(32, 4 * StepShape<S, VARIANT>::kMinBlocks)
+    k_step_shell_rows(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
+                      const __grid_constant__ StepParams p, int* __restrict__ status) {
+  const int w = blockIdx.x;
+  const int seg = w % p.row_segs, r = w / p.row_segs;
+  Cell cl;
+  shell_row(r, p, cl.y, cl.z);
+  const int x0 = seg * 32, x = x0 + (threadIdx.x & 31);
+  const bool valid = x < p.nx;
+  cl.x = valid ? x : p.nx - 1;
+  cl.c = (cl.z * p.ny + cl.y) * p.nx + cl.x;
+  const bool xfast = x0 >= p.ix0 && min(x0 + 31, p.nx - 1) < p.ix0 + p.ixn;
+  step_cell<L, S, false, VARIANT, kPathShellRow, WALLS>(src, dst, p, status, cl, valid, xfast);
 }
 
 // Shell cells (rows whose y or z lies outside the interior box): z-boundary planes, then the

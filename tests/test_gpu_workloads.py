@@ -95,3 +95,29 @@ def test_shear_wave_128_cube_equals_the_1d_oracle(storage, tol, eta_over_s):
     rate_g = -np.polyfit(ts[1:], np.log(amp_g[1:]), 1)[0]
     print("shear %s eta/s %.2f: decay per step oracle %.6e gpu %.6e" % (storage, eta_over_s, rate_o, rate_g))
     assert rate_o > 0 and abs(rate_g - rate_o) <= 1e-3 * rate_o
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f16dev", 5e-2)])
+def test_reduced_precision_over_1000_steps(storage, tol):
+    """The throughput case's recipe (random field, |v| <= 0.6, sigma_lnT = 0.2, uniform n,
+    eta/s = 0.1) on 64^3, 1000 steps: float storage (the autotuner's variant) stays within 1e-5
+    of the double-precision GPU path on n, eps and u; the half-deviation store's error stays
+    bounded."""
+    N = 64
+    n, T, u = gen.smooth_random_fields((N, N, N), seed=1, vmax=0.6, sigma_lnT=0.2, density="uniform")
+    res = {}
+    for st in ("f64", storage):
+        with RLB((N, N, N), order=3, storage=st, eta_over_s=0.1) as g:
+            g.init(n, T, u)
+            if st != "f64":
+                g.autotune(reps=2)
+            g.step(1000)
+            res[st] = g.moments()
+    ref, got = res["f64"], res[storage]
+    en = np.max(np.abs(got["n"] - ref["n"]) / np.abs(ref["n"]))
+    ee = np.max(np.abs(got["eps"] - ref["eps"]) / np.abs(ref["eps"]))
+    uref = ref["U"][1:] / ref["U"][0]
+    ugot = got["U"][1:] / got["U"][0]
+    eu = np.max(np.abs(ugot - uref)) / max(np.max(np.abs(uref)), 0.01)
+    print("%s vs f64 after 1000 steps at 64^3: n %.2e eps %.2e u %.2e" % (storage, en, ee, eu))
+    assert max(en, ee, eu) < tol
