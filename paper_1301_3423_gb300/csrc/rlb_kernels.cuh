@@ -5,8 +5,13 @@
 //   moments N^mu, T^{mu nu} over mirror pairs         (Sec. II.D)
 //   Landau  T^{ab} U_b = eps U^a, n = U.N, T = eps/(3n) (Eq. (eigenproblem))
 //   tau'    from eta/s and T                           (Sec. II.D, Sec. III)
-//   f^eq    factored equilibrium, E(p0, t) with t = v.U/R   (App. B, Eq. (eq:equi3rd) / (eq:equi2nd))
+//   f^eq    E(p0, t), t = v.U/R, as a cubic in t per energy level (App. B, Eq. (eq:equi3rd) /
+//           (eq:equi2nd) regrouped)
 //   collide f_i - (U0 - t_i)/tau' (f_i - w_i E_i)      one write per population
+// The cells of a step are split over two launches: rows whose y and z are interior (constant
+// offsets, or x wrapped only, per 32-aligned warp segment) and the boundary rows (k_step_shell_rows;
+// k_step_shell per cell for lattices shorter than the stencil reach).  Batched steps use the same
+// split across many lattices (k_step_batch).
 //
 // The quadrature is a compile-time table (generated rlb_quadrature.h), so every per-population
 // constant (velocity components, energy, weight, mirror partner) is an immediate.
