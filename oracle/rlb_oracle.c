@@ -32,6 +32,14 @@
  * Conventions: lattice units delta x = delta t' = 1, metric diag(+,-,-,-),
  * p_i^mu = p0_i (1, v_i / R) (Eq. (eq:mrecon2)).  Populations are stored f[i][z][y][x].
  * The stored state is post-collision; a step is pull, then collide.
+ *
+ * Pins (tests/test_oracle_*.py, tests/test_lattice.py): the equilibrium against the closed-form
+ * Maxwell-Juttner moments and the appendix forms, Landau matching against a dense eigen-solver,
+ * one step against an independent numpy step, conservation, stationarity, the shear-wave rate,
+ * the Riemann impulse, bounce-back conservation and no-slip.  The weight tables are read from
+ * lattice/*.txt, rebuilt from the moment conditions of Eqs. (eqs:eqs) because the paper does not
+ * print its own: results that depend on which valid table is used (beyond the moment conditions)
+ * are parity unpinned against the paper.
  */
 #include <math.h>
 #include <stddef.h>
