@@ -64,8 +64,10 @@ struct StoreF32 {
   using T = float;
   using A = float;
   static constexpr bool kKeep = true;   // all populations of a cell live in registers
+  // Each population is read once per step: cached in L2 only, leaving L1 to the register spills
+  // (measured 4.7 % faster at 256^3 than loads that also allocate in L1).
   template <class L, int I>
-  __device__ static __forceinline__ A load(const T* p, const StepParams&) { return __ldg(p); }
+  __device__ static __forceinline__ A load(const T* p, const StepParams&) { return __ldcg(p); }
   template <class L, int I>
   __device__ static __forceinline__ void store(T* p, A v, const StepParams&) { *p = v; }
   template <class L, int I>
