@@ -500,7 +500,7 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                      "peak_source": peak_src, "algorithmic_bytes_per_step": algo_bytes,
-                     "kernel": "k_step_interior + k_step_shell <Quad3, StoreF32, variant %d>" % variant,
+                     "kernel": "k_step_interior + k_step_shell_rows <Quad3, StoreF32, variant %d>" % variant,
                      "step_ms": per_step_s * 1e3, "launches_per_step": launches / args.steps},
         "cpu_baseline": cb,
         "e2e": e2e,
