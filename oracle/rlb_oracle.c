@@ -37,9 +37,9 @@
  * Maxwell-Juttner moments and the appendix forms, Landau matching against a dense eigen-solver,
  * one step against an independent numpy step, conservation, stationarity, the shear-wave rate,
  * the Riemann impulse, bounce-back conservation and no-slip.  The weight tables are read from
- * lattice/*.txt, rebuilt from the moment conditions of Eqs. (eqs:eqs) because the paper does not
- * print its own: results that depend on which valid table is used (beyond the moment conditions)
- * are parity unpinned against the paper.
+ * the lattice/ text files, rebuilt from the moment conditions of Eqs. (eqs:eqs) because the paper
+ * does not print its own: results that depend on which valid table is used (beyond the moment
+ * conditions) are parity unpinned against the paper.
  */
 #include <math.h>
 #include <stddef.h>
