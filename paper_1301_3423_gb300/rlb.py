@@ -356,8 +356,9 @@ class RLB:
 
 
 class Batch:
-    """rlb_batch_*: step many RLB contexts (same order and storage) together in one persistent
-    kernel per step over a shared tile queue, optionally replaying CUDA graphs of several steps."""
+    """rlb_batch_*: step many RLB contexts (same order and storage) together, each time step two
+    persistent launches over shared tile queues (the members' interior rows, then their boundary
+    cells), optionally replaying CUDA graphs of several steps."""
 
     def __init__(self, order=3, storage="f32", stream=None):
         self._lib = load()

@@ -1,4 +1,4 @@
-"""Batched stepping: uneven instances in one persistent kernel over a tile queue, with CUDA-graph step
+"""Batched stepping: uneven instances in persistent kernels over shared tile queues, with CUDA-graph step
 loops; each member's result equals its solo run."""
 import numpy as np
 import pytest
