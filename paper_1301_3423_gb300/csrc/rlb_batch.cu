@@ -137,11 +137,14 @@ static rlb_status upload_table(rlb_batch* b, long nsteps, int* nmembers, int* to
     d.parity0 = m.ctx->cur;
     d.steps_left = (int)std::min<long>(m.steps_left, nsteps);
     if (d.p.has_wall) b->walls = 1;
-    // row tiles: 4 row-kernel warps; shell tiles: kStepThreads shell cells
+    // row tiles: 4 row-kernel warps; shell tiles: 4 shell-row warps (kStepThreads shell cells for
+    // members that need the modulo wrap)
     d.row_tile_begin = (int)row_tm.size();
     row_tm.resize(row_tm.size() + (d.p.int_warps + kStepThreads / 32 - 1) / (kStepThreads / 32), (int)t.size());
     d.shell_tile_begin = (int)shell_tm.size();  // shifted by the row tiles below
-    shell_tm.resize(shell_tm.size() + (d.p.shell_cells + kStepThreads - 1) / kStepThreads, (int)t.size());
+    const int shell_tiles = d.p.general ? (d.p.shell_cells + kStepThreads - 1) / kStepThreads
+                                        : (d.p.shell_warps + kStepThreads / 32 - 1) / (kStepThreads / 32);
+    shell_tm.resize(shell_tm.size() + shell_tiles, (int)t.size());
     t.push_back(d);
   }
   b->row_tiles = (int)row_tm.size();

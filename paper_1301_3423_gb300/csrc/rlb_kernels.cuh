@@ -870,8 +870,9 @@ __global__ void __launch_bounds__(kStepThreads, StepShape<S, VARIANT>::kMinBlock
 // ---------------------------------------------------------------------------------------------
 // Batched step: many independent lattices (members) advance together.  Each time step is two
 // persistent launches, one over the members' row tiles (four row-kernel warps each: constant
-// offsets, or x wrapped only) and one over their shell tiles (kStepThreads shell cells each, every
-// coordinate wrapped): the decomposition of a solo step, so a member's populations are bitwise those
+// offsets, or x wrapped only) and one over their shell tiles (four shell-row warps each, or
+// kStepThreads shell cells each for members that need the modulo wrap): the decomposition of a
+// solo step, so a member's populations are bitwise those
 // of the same steps taken alone with the same variant, and each kernel carries one pull path.
 // Blocks take tiles from the launch's queue (an atomic counter); a tile's member comes from a
 // tile -> member table (row tiles first, then shell tiles), and a block copies a member's
@@ -917,12 +918,26 @@ __global__ void __launch_bounds__(kStepThreads, StepShape<S, VARIANT>::kMinBlock
           row_cell(w, threadIdx.x & 31, sp, cl, valid, fast);
           step_cell<L, S, false, VARIANT, kPathRow, WALLS>(sb, db, sp, m.status, cl, valid, fast);
         }
-      } else {
+      } else if (sp.general) {
+        // per cell, modulo wrap (a periodic axis shorter than the stencil reach)
         const int s = (tile - m.shell_tile_begin) * kStepThreads + threadIdx.x;
         const bool valid = s < sp.shell_cells;
         const Cell cl = shell_cell(valid ? s : sp.shell_cells - 1, sp);
-        if (sp.general) step_cell<L, S, true, VARIANT, kPathEdge, WALLS>(sb, db, sp, m.status, cl, valid);
-        else step_cell<L, S, false, VARIANT, kPathEdge, WALLS>(sb, db, sp, m.status, cl, valid);
+        step_cell<L, S, true, VARIANT, kPathEdge, WALLS>(sb, db, sp, m.status, cl, valid);
+      } else {
+        // four shell-row warps, as in k_step_shell_rows
+        const int w = (tile - m.shell_tile_begin) * (kStepThreads / 32) + (threadIdx.x >> 5);
+        if (w < sp.shell_warps) {  // whole warps only
+          const int seg = w % sp.row_segs, r = w / sp.row_segs;
+          Cell cl;
+          shell_row(r, sp, cl.y, cl.z);
+          const int x0 = seg * 32, x = x0 + (threadIdx.x & 31);
+          const bool valid = x < sp.nx;
+          cl.x = valid ? x : sp.nx - 1;
+          cl.c = (cl.z * sp.ny + cl.y) * sp.nx + cl.x;
+          const bool xfast = x0 >= sp.ix0 && min(x0 + 31, sp.nx - 1) < sp.ix0 + sp.ixn;
+          step_cell<L, S, false, VARIANT, kPathShellRow, WALLS>(sb, db, sp, m.status, cl, valid, xfast);
+        }
       }
     }
     __syncthreads();  // sp and s_tile are reused by the next tile
