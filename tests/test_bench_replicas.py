@@ -76,3 +76,16 @@ def test_reference_arm_under_torchrun_prints_one_line_from_rank_0():
     line = json.loads(lines[0])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_traffic_record_is_used_only_for_the_kernel_sources_it_was_taken_on(tmp_path, monkeypatch):
+    """roofline.traffic comes from profiles/step_f32_traffic.json only while the step kernels'
+    sources hash to the recorded digest and the variant, lattice and density match."""
+    bench = load_bench()
+    rec = json.load(open(os.path.join(ROOT, "profiles", "step_f32_traffic.json")))
+    assert rec["dram_bytes_per_step"] >= rec["algorithmic_bytes_per_step"] * 0.99
+    assert bench.recorded_traffic(rec["lattice"], rec["variant"], rec["density"]) == rec["dram_bytes_per_step"]
+    assert bench.recorded_traffic(rec["lattice"], rec["variant"] ^ 1, rec["density"]) is None
+    assert bench.recorded_traffic(rec["lattice"] // 2, rec["variant"], rec["density"]) is None
+    monkeypatch.setattr(bench, "kernel_sources_digest", lambda: "0" * 64)  # the kernels changed
+    assert bench.recorded_traffic(rec["lattice"], rec["variant"], rec["density"]) is None
