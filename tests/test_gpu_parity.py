@@ -117,9 +117,10 @@ def test_f64_interior_warps_match_oracle(order):
 @pytest.mark.parametrize("bc", ["periodic", "copyout_xy", "walls_xz"])
 def test_interior_and_shell_kernels_match_oracle(order, variant, bc):
     """72 x 20 x 24 cells.  The row kernel takes the rows with interior y and z in x segments
-    [0, 32) (x wraps), [32, 64) (constant offsets) and [64, 72) (partial warp, x wraps); the shell
-    kernel the z-boundary planes and y-boundary rows (every coordinate wraps, or x and y are
-    clamped for copy-out, or populations from beyond the x and z walls bounce back).  Double storage per population; float storage (variant 3) on the fields."""
+    [0, 32) (x wraps), [32, 64) (constant offsets) and [64, 72) (partial warp, x wraps); the
+    shell-row kernel takes the z-boundary planes and y-boundary rows, with per-population y and z
+    shifts for the whole warp (wrapped, or x and y clamped for copy-out, or reversed populations at
+    bounce-back walls).  Double storage per population; float storage (variant 3) on the fields."""
     lat = oracle.read_lattice(order)
     shape = (24, 20, 72)
     n, T, u = gen.smooth_random_fields(shape, seed=51, vmax=0.45, sigma_lnT=0.15, kmax=2)
