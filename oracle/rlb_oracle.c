@@ -36,7 +36,9 @@
  * Pins (tests/test_oracle_*.py, tests/test_lattice.py): the equilibrium against the closed-form
  * Maxwell-Juttner moments and the appendix forms, Landau matching against a dense eigen-solver,
  * one step against an independent numpy step, conservation, stationarity, the shear-wave rate,
- * the Riemann impulse, bounce-back conservation and no-slip.  The weight tables are read from
+ * the Riemann impulse, bounce-back conservation and no-slip, the reference-temperature relaxation
+ * time against a fixed tau', and the sampled one-step routine (ora_init_step_cells) against init
+ * plus one whole-lattice step at corners, face-adjacent and random cells for every boundary type.  The weight tables are read from
  * the lattice/ text files, rebuilt from the moment conditions of Eqs. (eqs:eqs) because the paper
  * does not print its own: results that depend on which valid table is used (beyond the moment
  * conditions) are parity unpinned against the paper.

@@ -320,3 +320,62 @@ def test_reference_temperature_scan():
     d = [np.max(np.abs(prof[(2, a)] - prof[(2, b)])) for a, b in ((1.0, 1.5), (1.5, 2.0), (2.0, 2.5), (2.5, 3.0),
                                                                    (3.0, 3.5))]
     assert np.all(np.diff(d[1:]) < 0) and d[-1] < 0.5 * d[0], d
+
+
+def edge_and_corner_cells(shape, rng, extra=24):
+    """Flat indices (x fastest) of the lattice's corners, of cells next to every face and of random
+    interior cells."""
+    nz, ny, nx = shape
+    pts = set()
+    for z in (0, 1, nz // 2, nz - 2, nz - 1):
+        for y in (0, 1, ny // 2, ny - 2, ny - 1):
+            for x in (0, 1, nx // 2, nx - 2, nx - 1):
+                pts.add((z % nz, y % ny, x % nx))
+    for _ in range(extra):
+        pts.add((int(rng.integers(nz)), int(rng.integers(ny)), int(rng.integers(nx))))
+    return np.array(sorted((z * ny + y) * nx + x for z, y, x in pts), dtype=np.int64)
+
+
+@pytest.mark.parametrize("order", [3, 2])
+@pytest.mark.parametrize("shape", [(11, 13, 17), (14, 8, 9)])
+@pytest.mark.parametrize("bc", [(0, 0, 0), (1, 0, 1), (2, 0, 2), (0, 2, 0), (2, 2, 2)])
+def test_init_step_cells_equals_init_then_one_step(order, shape, bc):
+    """The sampled one-step oracle (pull from the initial equilibrium, evaluated per source
+    population, then collide; Eq. (rlb:disc)) against the whole-lattice route: init on every cell,
+    one full step, read at the same cells.  Covers wrap, copy-out and the reversed population
+    beyond a bounce-back wall at corners and next to every face."""
+    lat = oracle.read_lattice(order)
+    nz, ny, nx = shape
+    n, T, u = gen.smooth_random_fields(shape, seed=31 + order, vmax=0.5, sigma_lnT=0.2, density="uniform")
+    o = oracle.OracleRLB(lat, nx, ny, nz, bc=bc, eta_over_s=0.1)
+    o.init(n, T, u)
+    o.step(1)
+    assert o.nonconv == 0
+    sample = edge_and_corner_cells(shape, np.random.default_rng(order * 100 + nx))
+    got = o.init_step_cells(n, T, u, sample)
+    ref = o.f.reshape(lat.q, -1)[:, sample].T
+    scale = lat.w[None, :] * np.max(n) / 2
+    assert np.max(np.abs(got - ref) / scale) <= 1e-14
+
+
+@pytest.mark.parametrize("order", [3, 2])
+@pytest.mark.parametrize("T_ref", [1.0, 2.5])
+def test_reference_temperature_relaxation_time(order, T_ref):
+    """tau_local_T = 0 takes tau' from the reference temperature T_ref (Sec. III): the same
+    mapping as a fixed tau' = 1/2 + 6 (eta/s) / (R kappa T_ref), on a lattice whose local T differs
+    from T_ref (the shock tube), and it differs from the local-T run."""
+    lat = oracle.read_lattice(order)
+    n, T, u = gen.riemann_tube(64)
+    kappa = 0.4 * 0.008 / HBARC
+    tau_ref = 0.5 + 6 * 0.1 / (lat.R * kappa * T_ref)
+    assert oracle.tau_prime(0.1, lat.R, T_ref) == pytest.approx(tau_ref, rel=1e-14)
+    runs = {}
+    for key, kw in (("ref", dict(eta_over_s=0.1, tau_local_T=0, T_ref=T_ref)), ("fixed", dict(tau_prime=tau_ref)),
+                    ("local", dict(eta_over_s=0.1, tau_local_T=1))):
+        o = oracle.OracleRLB(lat, 1, 1, 64, bc=(0, 0, 1), **kw)
+        o.init(n, T, u)
+        o.step(20)
+        runs[key] = o.f
+    scale = lat.w[:, None, None, None] * np.max(n) / 2
+    assert np.max(np.abs(runs["ref"] - runs["fixed"]) / scale) < 1e-13
+    assert np.max(np.abs(runs["ref"] - runs["local"]) / scale) > 1e-6
