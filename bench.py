@@ -114,7 +114,7 @@ class ClockSampler:
 
 # Sources that decide the step kernels' memory traffic: a DRAM-traffic record taken with ncu is
 # used only while these are byte-for-byte the ones it was taken on.
-TRAFFIC_SOURCES = ("rlb_kernels.cuh", "rlb_common.h", "rlb_inst_variant.cu")
+TRAFFIC_SOURCES = ("rlb_kernels.cuh", "rlb_pipe.cuh", "rlb_common.h", "rlb_inst_variant.cu", "rlb_inst_pipe.cu")
 
 
 def kernel_sources_digest():
@@ -125,10 +125,13 @@ def kernel_sources_digest():
     return h.hexdigest()
 
 
-def recorded_traffic(n_side, variant, density):
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "step_f32_traffic.json")
+
+
+def recorded_traffic(n_side, variant, density, path=None):
     """DRAM bytes (read + write) of one step from profiles/step_f32_traffic.json, or None when the
     record is missing or was taken on other kernel sources, another variant or lattice."""
-    path = os.path.join(ROOT, "profiles", "step_f32_traffic.json")
+    path = path or TRAFFIC_RECORD
     try:
         rec = json.load(open(path))
     except (OSError, ValueError):

@@ -88,8 +88,8 @@ typedef struct {
   double gamma_thr;   /* RLB_F32 / RLB_F16DEV only: cells whose Eckart Lorentz factor exceeds this
                          are solved in double (default 2.0) */
   double n_ref;       /* RLB_F16DEV only: reference density of the stored deviation (default 1.0) */
-  int step_variant;   /* float storage only: -1 = library default, or force a step-kernel variant
-                         (see rlb_autotune); ignored for RLB_F64 */
+  int step_variant;   /* -1 = library default, or force a step-kernel variant (see rlb_autotune);
+                         a variant that does not exist for the context falls back to the default */
   void* stream;       /* cudaStream_t to enqueue on; NULL = the default stream */
   /* Optional quadrature (Sec. II.C, App. A).  When q > 0 these arrays are compared with the
    * quadrature compiled into the library for this order and must match exactly (RLB_EINVAL
@@ -147,18 +147,25 @@ rlb_status rlb_get_populations(rlb_ctx* ctx, double* f, int on_device);
 rlb_status rlb_set_populations(rlb_ctx* ctx, const double* f, int on_device);
 
 /* Upper bound on the number of step-kernel variants. */
-#define RLB_MAX_VARIANTS 8
+#define RLB_MAX_VARIANTS 16
 
-/* Autotuner: time every step-kernel variant of this context on the context's own lattice and keep
- * the fastest for later rlb_step calls.  For float and half storage variants 0..3 differ in
- * arithmetic (bit 0: scalar, or mirror pairs in paired-FMA float2) and residency (bit 1: all
- * populations in registers at 2 or 3 resident blocks per SM).  Double storage has one.  Each
- * variant repeats one step from the current populations into the spare buffer `reps` times, so the
- * state does not change; this is allowed only before the first step after rlb_init
- * / rlb_set_populations (RLB_ESTATE otherwise).  *variant (may be NULL) receives the choice;
- * ms[RLB_MAX_VARIANTS] (may be NULL) the milliseconds per step of each variant (0 where a
- * variant does not exist).  Synchronises the stream.
- * Errors: RLB_EINVAL (reps < 1), RLB_ESTATE, RLB_ECUDA. */
+/* Autotuner: time every step-kernel variant that exists for this context and keep the fastest for
+ * later rlb_step calls.  Variants:
+ *   0..3  one cell per thread with all populations in registers, two launches per step (rows whose
+ *         y and z are interior, then the boundary rows); float and half storage only, except 0:
+ *         bit 0 = scalar or mirror pairs in paired-FMA float2 arithmetic, bit 1 = 2 or 3 resident
+ *         blocks per SM.  Double storage has variant 0, which reads its populations twice.
+ *   4..10 the pipelined kernel, one launch per step: a producer warp stages each tile's pulled
+ *         populations in shared memory with bulk copies and consumer warps relax the cells from
+ *         there; the variants differ in tile width (32 or 64 cells), consumer warps per block and
+ *         blocks per SM.  Every storage; only for lattices whose nx is a multiple of 16 bytes'
+ *         worth of populations (4 float, 8 half, 2 double).
+ * Each variant repeats one step from the current populations into the spare buffer `reps` times, so
+ * the state does not change; this is allowed only before the first step after rlb_init /
+ * rlb_set_populations (RLB_ESTATE otherwise).  *variant (may be NULL) receives the choice;
+ * ms[RLB_MAX_VARIANTS] (may be NULL) the milliseconds per step of each variant (0 where a variant
+ * does not exist for this context).  Synchronises the stream.
+ * Errors: RLB_EINVAL (reps < 1), RLB_ESTATE, RLB_ECUDA, RLB_ETIMEOUT. */
 rlb_status rlb_autotune(rlb_ctx* ctx, int reps, int* variant, double ms[RLB_MAX_VARIANTS]);
 
 /* ---------------------------------------------------------------------------------------------

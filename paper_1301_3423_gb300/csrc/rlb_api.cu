@@ -1,6 +1,7 @@
 // C ABI of librlb (declared in include/rlb.h): context management, validation, kernel launches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -115,7 +116,7 @@ static std::string validate(const rlb_params* p) {
   }
   if (!(p->gamma_thr >= 1.0)) return "gamma_thr must be >= 1";
   if (p->storage == RLB_F16DEV && !(p->n_ref > 0)) return "n_ref must be > 0";
-  if (p->step_variant < -1 || p->step_variant >= RLB_MAX_VARIANTS) return "step_variant must be -1 or 0..7";
+  if (p->step_variant < -1 || p->step_variant >= RLB_MAX_VARIANTS) return "step_variant must be -1 or 0..15";
   if (p->q > 0) {
     int q;
     const int *vel, *lev;
@@ -137,8 +138,8 @@ extern "C" size_t rlb_bytes_required(const rlb_params* p) {
   const size_t cells = (size_t)p->nx * p->ny * p->nz;
   const size_t q = p->order == 3 ? Quad3::Q : Quad2::Q;
   const size_t blocks = (cells + kMomThreads - 1) / kMomThreads;
-  return 2 * q * cells * storage_bytes(p->storage) + 6 * cells * sizeof(double) + 5 * blocks * sizeof(double) +
-         5 * sizeof(double) + kStatusWords * sizeof(int);
+  return 2 * (q * cells * storage_bytes(p->storage) + 2 * kPopGuardBytes) + 6 * cells * sizeof(double) +
+         5 * blocks * sizeof(double) + 5 * sizeof(double) + kStatusWords * sizeof(int);
 }
 
 template <class L>
@@ -154,6 +155,62 @@ static bool needs_general_wrap(const rlb_params& p) {
                 "boundary codes of the ABI and the kernels agree");
   return (p.bc[0] == RLB_BC_PERIODIC && p.nx < L::VMAX_X) || (p.bc[1] == RLB_BC_PERIODIC && p.ny < L::VMAX_Y) ||
          (p.bc[2] == RLB_BC_PERIODIC && p.nz < L::VMAX_Z);
+}
+
+// Shape of pipelined variant v (>= kNumRegVariants) on this context's lattice: the tiles, the
+// stages that fit the shared memory of one block, the launch.  False if the variant does not exist
+// or the lattice cannot use it (rows must start on 16-byte boundaries, at least one stage per
+// consumer group plus one in flight).
+static bool pipe_shape(const rlb_ctx* c, int v, PipeParams* pp, int* grid, int* threads, int* smem) {
+  if (v < kNumRegVariants || v >= kNumVariantsTotal) return false;
+  const PipeConfig& cf = kPipeConfigs[v - kNumRegVariants];
+  const int A = 16 / (int)c->elem;
+  if (c->sp.nx % A != 0 || c->sms <= 0) return false;
+  const long long stage = (long long)c->q * (cf.tx + A) * (long long)c->elem;
+  const long long budget = std::min<long long>(c->smem_optin, c->smem_per_sm / cf.ctas_per_sm - 1024);
+  const int nstage = (int)std::min<long long>(kPipeMaxStages, (budget - kPipeHeaderBytes) / stage);
+  const int groups = cf.cons_warps / (cf.tx / 32);
+  if (groups < 1 || nstage < groups + 1) return false;
+  PipeParams r{};
+  r.segs = (c->sp.nx + cf.tx - 1) / cf.tx;
+  const long long ntiles = (long long)r.segs * c->sp.ny * c->sp.nz;
+  if (ntiles > 0x7fffffffll) return false;
+  r.ntiles = (int)ntiles;
+  r.nstage = nstage;
+  r.groups = groups;
+  r.xperiodic = c->sp.bc[0] == kPeriodic ? 1 : 0;
+  if (pp) *pp = r;
+  if (grid) *grid = (int)std::min<long long>((long long)c->sms * cf.ctas_per_sm, ntiles);
+  if (threads) *threads = (cf.cons_warps + 1) * 32;
+  if (smem) *smem = (int)(kPipeHeaderBytes + nstage * stage);
+  return true;
+}
+
+static bool variant_available(const rlb_ctx* c, int v) {
+  if (v < 0) return false;
+  if (v < kNumRegVariants) return v < c->launch->step_variants;
+  return pipe_shape(c, v, nullptr, nullptr, nullptr, nullptr);
+}
+
+static rlb_status check_launch(rlb_ctx* c, cudaError_t e, const char* what);
+
+// One time step of the whole lattice with step-kernel variant v: the register kernels (two
+// launches: interior rows, then the shell) or the pipelined kernel (one launch).
+static rlb_status launch_step(rlb_ctx* c, int v) {
+  if (v >= kNumRegVariants) {
+    PipeParams pp;
+    int grid = 0, threads = 0, smem = 0;
+    if (!pipe_shape(c, v, &pp, &grid, &threads, &smem)) return fail(c, RLB_EINVAL, "step variant not available");
+    return check_launch(c,
+                        c->launch->pipe_step(c->buf[c->cur], c->buf[1 - c->cur], c->sp, pp, c->status,
+                                             kPipeConfigs[v - kNumRegVariants].tx, grid, threads, smem, c->stream),
+                        "pipelined step kernel");
+  }
+  rlb_status st = check_launch(
+      c, c->launch->step(c->buf[c->cur], c->buf[1 - c->cur], c->sp, c->status, c->general_wrap, v, c->stream),
+      "step kernels");
+  if (st == RLB_OK && c->sp.int_warps > 0 && c->sp.shell_cells > 0) ++c->launches;  // interior + shell
+  return st;
 }
 
 extern "C" rlb_status rlb_create(const rlb_params* p, rlb_ctx** out) {
@@ -198,8 +255,6 @@ extern "C" rlb_status rlb_create(const rlb_params* p, rlb_ctx** out) {
   static const Launchers* const table[2][3] = {{&launchers_o2_s0, &launchers_o2_s1, &launchers_o2_s2},
                                                {&launchers_o3_s0, &launchers_o3_s1, &launchers_o3_s2}};
   c->launch = table[p->order == 3 ? 1 : 0][p->storage];
-  c->variant = (p->step_variant >= 0 && p->step_variant < c->launch->step_variants) ? p->step_variant
-                                                                                      : kDefaultStepVariant;
   int vmax[3];
   if (p->order == 3) {
     fill_offsets<Quad3>(sp);
@@ -231,14 +286,27 @@ extern "C" rlb_status rlb_create(const rlb_params* p, rlb_ctx** out) {
 
   const size_t pop_bytes = (size_t)c->q * c->cells * c->elem;
   c->fblocks = (c->cells + kMomThreads - 1) / kMomThreads;
-  cudaError_t e = cudaSuccess;
-  for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&c->buf[b], pop_bytes);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) {
+    const int want = p->step_variant;
+    c->variant = (want >= 0 && variant_available(c, want)) ? want : kDefaultStepVariant;
+  }
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    e = cudaMalloc(&c->raw[b], pop_bytes + 2 * kPopGuardBytes);
+    if (e == cudaSuccess) {
+      c->buf[b] = static_cast<char*>(c->raw[b]) + kPopGuardBytes;
+      e = cudaMemsetAsync(c->raw[b], 0, pop_bytes + 2 * kPopGuardBytes, c->stream);
+    }
+  }
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->fields, 6 * (size_t)c->cells * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->partial, 5 * (size_t)c->fblocks * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->totals, 5 * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->status, kStatusWords * sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, kStatusWords * sizeof(int), c->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->buf[0], 0, pop_bytes, c->stream);
   if (e != cudaSuccess) {
     const rlb_status st = (e == cudaErrorMemoryAllocation) ? RLB_ENOMEM : RLB_ECUDA;
     cudaGetLastError();
@@ -253,7 +321,7 @@ extern "C" rlb_status rlb_destroy(rlb_ctx* c) {
   if (!c) return RLB_OK;
   if (c->stream || c->buf[0]) cudaStreamSynchronize(c->stream);
   for (int b = 0; b < 2; ++b)
-    if (c->buf[b]) cudaFree(c->buf[b]);
+    if (c->raw[b]) cudaFree(c->raw[b]);
   if (c->fields) cudaFree(c->fields);
   if (c->partial) cudaFree(c->partial);
   if (c->totals) cudaFree(c->totals);
@@ -279,6 +347,10 @@ static rlb_status read_status(rlb_ctx* c) {
   if (st[kStatusBadInit] > 0) {
     RLB_CUDA(c, cudaMemsetAsync(c->status, 0, kStatusWords * sizeof(int), c->stream));
     return fail(c, RLB_EINVAL, std::to_string(st[kStatusBadInit]) + " cells with invalid initial fields");
+  }
+  if (st[kStatusTimeout] > 0) {
+    RLB_CUDA(c, cudaMemsetAsync(c->status, 0, kStatusWords * sizeof(int), c->stream));
+    return fail(c, RLB_ETIMEOUT, std::to_string(st[kStatusTimeout]) + " bounded device-side waits ran out");
   }
   if (st[kStatusNonconv] > 0) {
     RLB_CUDA(c, cudaMemsetAsync(c->status, 0, kStatusWords * sizeof(int), c->stream));
@@ -318,12 +390,8 @@ extern "C" rlb_status rlb_step(rlb_ctx* c, long nsteps) {
   if (!c) return RLB_EINVAL;
   if (nsteps < 0) return fail(c, RLB_EINVAL, "nsteps < 0");
   for (long s = 0; s < nsteps; ++s) {
-    rlb_status st = check_launch(c,
-                                 c->launch->step(c->buf[c->cur], c->buf[1 - c->cur], c->sp, c->status,
-                                                 c->general_wrap, c->variant, c->stream),
-                                 "step kernels");
+    rlb_status st = launch_step(c, c->variant);
     if (st != RLB_OK) return st;
-    if (c->sp.int_warps > 0 && c->sp.shell_cells > 0) ++c->launches;  // interior + shell
     c->cur = 1 - c->cur;
     c->have_prev = true;
     ++c->steps;
@@ -341,14 +409,12 @@ extern "C" rlb_status rlb_autotune(rlb_ctx* c, int reps, int* variant, double ms
   double best = 1e300;
   int choice = c->variant;
   double t[RLB_MAX_VARIANTS] = {0};
-  for (int v = 0; v < c->launch->step_variants; ++v) {
+  for (int v = 0; v < kNumVariantsTotal && v < RLB_MAX_VARIANTS; ++v) {
+    if (!variant_available(c, v)) continue;
     // warm-up launch, then the timed repetitions; every launch recomputes the same next state
     for (int r = 0; r <= reps; ++r) {
       if (r == 1) RLB_CUDA(c, cudaEventRecord(e0, c->stream));
-      rlb_status st = check_launch(c,
-                                   c->launch->step(c->buf[c->cur], c->buf[1 - c->cur], c->sp, c->status,
-                                                   c->general_wrap, v, c->stream),
-                                   "step kernel");
+      rlb_status st = launch_step(c, v);
       if (st != RLB_OK) return st;
     }
     RLB_CUDA(c, cudaEventRecord(e1, c->stream));

@@ -8,6 +8,28 @@ constexpr int kMomThreads = 128;     // threads per block of the fields kernel
 constexpr int kReduceThreads = 256;  // threads of the single-block second reduction pass
 constexpr int kDefaultStepVariant = 0;  // step-kernel variant before autotuning (float storage)
 
+// Step-kernel variants.  0..3: one cell per thread with all populations in registers (float
+// storages; double storage has variant 0 only, which reads its populations twice).  4 and up: the
+// pipelined kernel (k_step_pipe) in the shapes of kPipeConfigs, for every storage, on lattices whose
+// rows start on 16-byte boundaries.
+constexpr int kNumRegVariants = 4;
+struct PipeConfig {
+  int tx;           // tile width in cells (32 or 64; TX / 32 consumer warps per tile)
+  int cons_warps;   // consumer warps per block
+  int ctas_per_sm;  // resident blocks per SM (the shared memory is split between them)
+};
+constexpr PipeConfig kPipeConfigs[] = {{32, 8, 1}, {32, 4, 2}, {32, 6, 1}, {64, 8, 1},
+                                       {64, 4, 1}, {32, 4, 1}, {32, 10, 1}};
+constexpr int kNumPipeConfigs = sizeof(kPipeConfigs) / sizeof(kPipeConfigs[0]);
+constexpr int kNumVariantsTotal = kNumRegVariants + kNumPipeConfigs;
+constexpr int kPipeMaxStages = 16;
+constexpr int kPipeMaxConsumerWarps = 12;  // launch bound of k_step_pipe
+constexpr int kPipeHeaderBytes = 1024;  // mbarriers (2 x 16 x 8 B) and the per-population velocity table
+// Bytes of slack before and after every population buffer: the pipelined kernel's copies of a row
+// segment next to a lattice end may start up to one granule before the row and end up to one tile
+// plus the stencil reach after it.
+constexpr int kPopGuardBytes = 1024;
+
 // ---------------------------------------------------------------------------------------------
 // launch parameters
 // ---------------------------------------------------------------------------------------------
@@ -40,7 +62,19 @@ struct StepParams {
 // per-axis boundary codes, as in rlb_bc
 enum : int { kPeriodic = 0, kCopyOut = 1, kBounceBack = 2 };
 
-enum : int { kStatusNonconv = 0, kStatusBadInit = 1, kStatusWords = 4 };
+// status words: cell updates without a Landau frame, cells with invalid initial fields, bounded
+// device-side waits that ran out
+enum : int { kStatusNonconv = 0, kStatusBadInit = 1, kStatusTimeout = 2, kStatusWords = 4 };
+
+// Launch shape of a pipelined step (k_step_pipe): tiles are TX-cell segments of the lattice rows,
+// tile t = row * segs + seg, block b takes tiles b, b + grid, ...
+struct PipeParams {
+  int ntiles;     // segs * ny * nz
+  int segs;       // tiles per row, ceil(nx / TX)
+  int nstage;     // shared-memory stages per block (<= 16)
+  int groups;     // consumer groups per block (TX / 32 warps each)
+  int xperiodic;  // x is periodic: the producer resolves the wrap with split copies
+};
 
 // One lattice of a batched step (see k_step_batch).
 struct BatchMember {

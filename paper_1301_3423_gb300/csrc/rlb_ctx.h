@@ -13,6 +13,7 @@ struct rlb_ctx {
   int q = 0;
   int cells = 0;
   size_t elem = 0;
+  void* raw[2] = {nullptr, nullptr};  // allocations: kPopGuardBytes, the buffer, kPopGuardBytes
   void* buf[2] = {nullptr, nullptr};
   int cur = 0;              // buf[cur] holds the current (post-collision) state
   bool have_prev = false;   // buf[1 - cur] holds the state the last step pulled from
@@ -27,6 +28,7 @@ struct rlb_ctx {
   int* status = nullptr;      // kStatusWords
   int fblocks = 0;
   const rlb::Launchers* launch = nullptr;
-  int variant = 0;            // step-kernel variant (float storage)
+  int variant = 0;            // step-kernel variant (kNumRegVariants register kernels, then pipelined shapes)
+  int sms = 0, smem_per_sm = 0, smem_optin = 0;  // device: SMs, shared memory per SM, per block (opt-in)
   std::string err;
 };

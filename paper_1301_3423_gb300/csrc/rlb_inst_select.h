@@ -42,6 +42,15 @@ constexpr int kVariants = kFloat ? kNumVariants : 1;
   cudaError_t RLB_VFN(batch, v)(const BatchMember* m, const int* tm, int row_tiles, int shell_tiles, int li, \
                                 int* counters, int walls, int grid, cudaStream_t s);                                                             \
   int RLB_VFN(occupancy, v)();
+// Pipelined step kernel per tile width (rlb_inst_pipe.cu, one unit per width).
+#define RLB_PFN(fn, tx) RLB_CAT7(fn, _o, RLB_INST_ORDER, _s, RLB_INST_STORAGE, _x, tx)
+#define RLB_DECLARE_PIPE(tx)                                                                                   \
+  cudaError_t RLB_PFN(pipe, tx)(const void* src, void* dst, const StepParams& p, const PipeParams& pp, int* status, \
+                                int grid, int threads, int smem, cudaStream_t s);
+RLB_DECLARE_PIPE(32)
+RLB_DECLARE_PIPE(64)
+#undef RLB_DECLARE_PIPE
+
 RLB_DECLARE_VARIANT(0)
 RLB_DECLARE_VARIANT(1)
 RLB_DECLARE_VARIANT(2)

@@ -654,6 +654,53 @@ __device__ __forceinline__ void collide_f2(const Landau<float>& lw, float T, flo
 // ---------------------------------------------------------------------------------------------
 // the fused step kernel
 // ---------------------------------------------------------------------------------------------
+// Compiler-level barrier: values read from memory before it are read again after it.
+__device__ __forceinline__ void reload_barrier() { asm volatile("" ::: "memory"); }
+
+// Moments, Landau matching, relaxation time, equilibrium and collision of one cell (steps a2-a7)
+// whose pulled populations get(I) returns (deviations d_i for half-deviation storage); store(I, v)
+// writes post-collision population I.  Shared by every step kernel, whatever it pulls from
+// (registers, global memory or a shared-memory stage).  RELOAD = true makes the collision read
+// every population again through get instead of keeping the moment pass's values in registers
+// (for populations staged in shared memory).  A cell without a Landau frame is counted in status
+// (valid lanes only) and streamed without collision.
+template <class L, class S, bool PACKED, bool RELOAD = false, class Get, class Store>
+__device__ __forceinline__ void relax_cell(Get&& get, Store&& store, const StepParams& p, int* __restrict__ status,
+                                           const bool valid) {
+  using A = typename S::A;
+  constexpr bool DEV = std::is_same<S, StoreF16Dev>::value;
+  const A c_dev = DEV ? A(p.half_nref) : A(0);
+  auto get2 = [&](auto I) -> float2 {
+    constexpr int i = decltype(I)::value;
+    return make_float2((float)get(ic<i>{}), (float)get(ic<i + 1>{}));
+  };
+  Mom<A> m;
+  if constexpr (PACKED) m = moments_f2<L, DEV>(get2, (float)c_dev);
+  else m = moments<L, A, DEV>(get, c_dev);
+  if constexpr (RELOAD) reload_barrier();
+  const Landau<A> lw = landau_step<A>(m, p);
+  if (!lw.ok) {
+    // no Landau frame: record it and stream the populations without collision
+    if (valid) {
+      atomicAdd(&status[kStatusNonconv], 1);
+      static_for<L::Q>([&](auto I) { store(I, get(I)); });
+    }
+    return;
+  }
+  const A T = lw.eps / (A(3) * lw.n);
+  const A inv_tau = A(1) / tau_prime<A>(T, p);
+  if constexpr (PACKED) {
+    auto put2 = [&](auto I, float2 v) {
+      constexpr int i = decltype(I)::value;
+      store(ic<i>{}, v.x);
+      store(ic<i + 1>{}, v.y);
+    };
+    collide_f2<L, DEV>(lw, T, inv_tau, get2, put2, (float)c_dev);
+  } else {
+    collide<L, A, DEV>(lw, T, inv_tau, get, store, c_dev);
+  }
+}
+
 // Step-kernel variants for float arithmetic.  Every population is pulled once and all populations
 // of a cell stay in registers.
 //   bit 0: scalar arithmetic (0) or mirror pairs in float2 with paired FMA (1);
@@ -701,7 +748,6 @@ __device__ __forceinline__ void step_cell(const typename S::T* __restrict__ src,
   // Half-deviation storage works in deviation space: the values in flight are d_i = f_i / w_i - c
   // as stored, and the moments and collision take the weights and c into their constants.
   constexpr bool DEV = std::is_same<S, StoreF16Dev>::value;
-  const A c_dev = DEV ? A(p.half_nref) : A(0);
   auto ld = [&](auto I, const ST* ptr) -> A {
     constexpr int i = decltype(I)::value;
     if constexpr (DEV) return S::template load_dev<L, i>(ptr, p);
@@ -733,37 +779,8 @@ __device__ __forceinline__ void step_cell(const typename S::T* __restrict__ src,
     if constexpr (KEEP) return fk[decltype(I)::value];
     else return load(I);
   };
-  auto get2 = [&](auto I) -> float2 {
-    constexpr int i = decltype(I)::value;
-    return make_float2((float)get(ic<i>{}), (float)get(ic<i + 1>{}));
-  };
-
-  Mom<A> m;
-  if constexpr (PACKED) m = moments_f2<L, DEV>(get2, (float)c_dev);
-  else m = moments<L, A, DEV>(get, c_dev);
-  const Landau<A> lw = landau_step<A>(m, p);
-  if (!lw.ok) {
-    // no Landau frame: record it and stream the populations without collision
-    if (valid) {
-      atomicAdd(&status[kStatusNonconv], 1);
-      static_for<L::Q>([&](auto I) { store(I, get(I)); });
-    }
-    return;
-  }
-  const A T = lw.eps / (A(3) * lw.n);
-  const A inv_tau = A(1) / tau_prime<A>(T, p);
-  if constexpr (PACKED) {
-    auto put2 = [&](auto I, float2 v) {
-      constexpr int i = decltype(I)::value;
-      store(ic<i>{}, v.x);
-      store(ic<i + 1>{}, v.y);
-    };
-    collide_f2<L, DEV>(lw, T, inv_tau, get2, put2, (float)c_dev);
-  } else {
-    collide<L, A, DEV>(lw, T, inv_tau, get, store, c_dev);
-  }
+  relax_cell<L, S, PACKED>(get, store, p, status, valid);
 }
-
 
 // Cell of lane `lane` in row-kernel warp w (see k_step_interior).
 __device__ __forceinline__ void row_cell(int w, int lane, const StepParams& p, Cell& cl, bool& valid, bool& fast) {

@@ -5,6 +5,7 @@
 
 namespace rlb {
 struct StepParams;
+struct PipeParams;
 struct BatchMember;
 
 struct Launchers {
@@ -24,6 +25,9 @@ struct Launchers {
                             int launch_index, int* counters, int variant, int walls, int grid, cudaStream_t s);
   // resident blocks per SM of the batched step for a variant
   int (*batch_blocks_per_sm)(int variant);
+  // one time step of the pipelined kernel with tile width tx (32 or 64)
+  cudaError_t (*pipe_step)(const void* src, void* dst, const StepParams& p, const PipeParams& pp, int* status, int tx,
+                           int grid, int threads, int smem, cudaStream_t s);
 };
 
 #define RLB_DECLARE_LAUNCHERS(ORDER, STORAGE) extern const Launchers launchers_o##ORDER##_s##STORAGE;

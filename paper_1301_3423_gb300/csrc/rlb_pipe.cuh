@@ -1,0 +1,269 @@
+// Pipelined step kernel: the pull of Eq. (rlb:disc) staged through shared memory by the bulk-copy
+// (TMA) engine, with warp-specialised producer and consumer warps (sm_90+ PTX: mbarrier,
+// cp.async.bulk).
+//
+// A tile is one 32- or 64-cell segment of a lattice row (fixed y, z; x0 a multiple of the tile
+// width TX).  For every population i the cells x0 .. x0 + TX - 1 pull from the row
+// (y - vy_i, z - vz_i) at x - vx_i, i.e. from one contiguous run of the source plane.  The
+// producer warp copies that run, widened to 16-byte boundaries, into the tile's stage with one
+// bulk copy per population (cp.async.bulk, completion counted on the stage's mbarrier).  y and z
+// are resolved per row by the producer (periodic wrap or copy-out clamp); a periodic x is resolved
+// by splitting the run at the lattice ends into copies of whole 16-byte units.  Everything the
+// copies cannot express (a copy-out or bounce-back x, the reversed population beyond a y or z
+// wall) is patched in shared memory by the consumer warp before it reads the stage.
+//
+// Consumer warps own one 32-cell part of a tile each and read population i of lane x at the
+// compile-time offset i * BX + r_i + x of the stage (r_i = -vx_i mod the copy granule), twice:
+// once for the moments and once for the collision, whose result goes straight to global memory
+// with one coalesced store per population.  The populations never sit in registers as a whole,
+// so a consumer needs ~100 registers instead of Q + ~40, and the loads that feed a tile are issued
+// by one producer lane per population instead of 32 lanes each computing an address.
+//
+// Stages form a ring of NSTAGE slots per block: tile k of a block goes to stage k % NSTAGE and to
+// consumer group k % groups.  full[s] completes when the copies of the stage's tile have landed;
+// empty[s] when every consumer warp of that tile has finished reading it.  Every wait is bounded
+// (kPipeWaitNs); a wait that runs out counts in status[kStatusTimeout], and the producer then waits
+// (bounded) for the copies it has in flight before it returns.
+#pragma once
+
+#include <stdint.h>
+
+#include "rlb_kernels.cuh"
+
+namespace rlb {
+
+constexpr int kPipeMaxThreads = (kPipeMaxConsumerWarps + 1) * 32;
+constexpr unsigned long long kPipeWaitNs = 2000000000ull;  // 2 s
+
+// Geometry of one staged row for storage S and tile width TX.
+template <class S, int TX>
+struct PipeShape {
+  using T = typename S::T;
+  static constexpr int A = 16 / (int)sizeof(T);  // elements per 16-byte copy granule
+  static constexpr int BX = TX + A;              // the tile plus the slack of rounding down to a granule
+  static constexpr int ROW_BYTES = BX * (int)sizeof(T);
+  static_assert(ROW_BYTES % 16 == 0, "bulk copies move whole 16-byte units");
+};
+
+// -------------------------------------------------------------------------------------------------
+// PTX helpers (shared-memory mbarrier and bulk copy)
+// -------------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the phase of parity `parity` to complete; false after kPipeWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer_ns() - t0 > kPipeWaitNs) return false;
+  }
+}
+
+// Bulk copy global -> shared of `bytes` (a multiple of 16; both addresses 16-byte aligned), counted
+// on `bar` as transaction bytes.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Orders this thread's generic-proxy shared-memory writes before later bulk copies into them.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// -------------------------------------------------------------------------------------------------
+// the kernel
+// -------------------------------------------------------------------------------------------------
+// Source row of a pull along y or z: periodic wrap (any length) or copy-out clamp.  Beyond a
+// bounce-back wall any in-range row will do: the consumer replaces those populations.
+__device__ __forceinline__ int pipe_src_row(int s, int n, int bc) {
+  if (bc == kPeriodic) {
+    s %= n;
+    return s < 0 ? s + n : s;
+  }
+  return min(max(s, 0), n - 1);
+}
+
+template <class L, class S, int TX, bool WALLS>
+__global__ void __launch_bounds__(kPipeMaxThreads, 1)
+    k_step_pipe(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
+                const __grid_constant__ StepParams p, const __grid_constant__ PipeParams pp,
+                int* __restrict__ status) {
+  using T = typename S::T;
+  using A = typename S::A;
+  using Sh = PipeShape<S, TX>;
+  constexpr int BX = Sh::BX, AL = Sh::A, WPT = TX / 32;
+  constexpr int kStageElems = L::Q * BX;
+  constexpr bool PACKED = std::is_same<A, float>::value;
+  constexpr bool DEV = std::is_same<S, StoreF16Dev>::value;
+  static_assert(TX % 32 == 0 && TX >= 32, "tile width");
+
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* empty = full + kPipeMaxStages;
+  char4* sv = reinterpret_cast<char4*>(smem + 2 * 8 * kPipeMaxStages);
+  T* const stage0 = reinterpret_cast<T*>(smem + kPipeHeaderBytes);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cons_warps = pp.groups * WPT;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < pp.nstage; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], WPT);
+    }
+    static_for<L::Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      constexpr signed char vx = L::VX[i], vy = L::VY[i], vz = L::VZ[i];
+      sv[i] = make_char4(vx, vy, vz, 0);
+    });
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const long long G = gridDim.x;
+
+  if (warp == cons_warps) {
+    // ---- producer warp: one bulk copy (or a few, at a periodic x end) per population and tile
+    int k = 0;
+    bool ok = true;
+    for (;; ++k) {
+      const long long t = blockIdx.x + (long long)k * G;
+      if (t >= pp.ntiles) break;
+      const int s = k % pp.nstage;
+      if (k >= pp.nstage && !mbar_wait(&empty[s], (uint32_t)((k / pp.nstage) - 1) & 1u)) {
+        ok = false;
+        break;
+      }
+      if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)(kStageElems * sizeof(T)));
+      __syncwarp();
+      const int seg = (int)(t % pp.segs), row = (int)(t / pp.segs);
+      const int y = row % p.ny, z = row / p.ny;
+      const int x0 = seg * TX;
+      T* const st = stage0 + (size_t)s * kStageElems;
+      for (int i = lane; i < L::Q; i += 32) {
+        const char4 v = sv[i];
+        const int ys = pipe_src_row(y - v.y, p.ny, p.bc[1]);
+        const int zs = pipe_src_row(z - v.z, p.nz, p.bc[2]);
+        const T* rowp = src + (long long)i * p.cells + ((long long)zs * p.ny + ys) * p.nx;
+        const int xs = (x0 - v.x) & ~(AL - 1);  // round down to a granule (two's complement: floor)
+        T* d = st + i * BX;
+        if (pp.xperiodic) {
+          // split [xs, xs + BX) at multiples of nx; each piece is whole granules of one period
+          int a = xs;
+          const int e = xs + BX;
+          while (a < e) {
+            const int per = (a >= 0) ? a / p.nx : -((-a + p.nx - 1) / p.nx);
+            const int pe = min(e, (per + 1) * p.nx);
+            bulk_g2s(d + (a - xs), rowp + (a - per * p.nx), (uint32_t)((pe - a) * sizeof(T)), &full[s]);
+            a = pe;
+          }
+        } else {
+          // x beyond the ends reads neighbouring memory (guard bytes around every buffer); the
+          // consumer patches those cells
+          bulk_g2s(d, rowp + xs, (uint32_t)Sh::ROW_BYTES, &full[s]);
+        }
+      }
+    }
+    if (!ok) {
+      if (lane == 0) atomicAdd(&status[kStatusTimeout], 1);
+      // let the copies already issued land before the block's shared memory goes away
+      for (int j = max(0, k - pp.nstage); j < k; ++j) mbar_wait(&full[j % pp.nstage], (uint32_t)(j / pp.nstage) & 1u);
+    }
+    return;
+  }
+  if (warp > cons_warps) return;
+
+  // ---- consumer warps: lane x of part wt of the tile is cell x0 + 32 wt + x
+  const int group = warp / WPT, wt = warp % WPT;
+  for (int k = group;; k += pp.groups) {
+    const long long t = blockIdx.x + (long long)k * G;
+    if (t >= pp.ntiles) break;
+    const int s = k % pp.nstage;
+    if (!mbar_wait(&full[s], (uint32_t)(k / pp.nstage) & 1u)) {
+      if (lane == 0) atomicAdd(&status[kStatusTimeout], 1);
+      return;
+    }
+    const int seg = (int)(t % pp.segs), row = (int)(t / pp.segs);
+    Cell cl;
+    cl.y = row % p.ny;
+    cl.z = row / p.ny;
+    const int x0 = seg * TX;
+    const int x = x0 + wt * 32 + lane;
+    const bool valid = x < p.nx;
+    cl.x = valid ? x : p.nx - 1;
+    cl.c = (cl.z * p.ny + cl.y) * p.nx + cl.x;
+    T* const lb = stage0 + (size_t)s * kStageElems + wt * 32 + lane;
+
+    // patch what the copies could not express (warp-uniform test)
+    bool patch = !pp.xperiodic && (x0 < L::VMAX_X || x0 + TX - 1 + L::VMAX_X >= p.nx);
+    if constexpr (WALLS)
+      patch = patch || (p.bc[1] == kBounceBack && (cl.y < L::VMAX_Y || cl.y >= p.ny - L::VMAX_Y)) ||
+              (p.bc[2] == kBounceBack && (cl.z < L::VMAX_Z || cl.z >= p.nz - L::VMAX_Z));
+    if (patch) {
+      static_for<L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int vx = L::VX[i];
+        constexpr int r = ((-vx) % AL + AL) % AL;
+        bool need = false;
+        if constexpr (WALLS) need = p.has_wall && beyond_wall<L, i>(cl, p);
+        if constexpr (vx != 0) need = need || (!pp.xperiodic && (unsigned)(cl.x - vx) >= (unsigned)p.nx);
+        if (need) lb[i * BX + r] = src[pull_index<L, i, true, WALLS>(cl, p)];
+      });
+      fence_proxy_async_smem();
+      __syncwarp();
+    }
+
+    auto get = [&](auto I) -> A {
+      constexpr int i = decltype(I)::value;
+      constexpr int r = ((-L::VX[i]) % AL + AL) % AL;
+      const T v = lb[i * BX + r];
+      if constexpr (DEV) return __half2float(v);
+      else return (A)v;
+    };
+    T* const out = dst + cl.c;
+    auto store = [&](auto I, A v) {
+      constexpr int i = decltype(I)::value;
+      if (valid) {
+        if constexpr (DEV) S::template store_dev<L, i>(out + (long long)i * p.cells, v, p);
+        else S::template store<L, i>(out + (long long)i * p.cells, v, p);
+      }
+    };
+    relax_cell<L, S, PACKED, true>(get, store, p, status, valid);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+}
+
+}  // namespace rlb

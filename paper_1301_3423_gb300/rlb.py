@@ -16,8 +16,10 @@ RLB_OK, RLB_EINVAL, RLB_ENOMEM, RLB_ECUDA, RLB_ENONCONV, RLB_ENAN, RLB_ETIMEOUT,
 STATUS_NAMES = ["RLB_OK", "RLB_EINVAL", "RLB_ENOMEM", "RLB_ECUDA", "RLB_ENONCONV", "RLB_ENAN", "RLB_ETIMEOUT",
                 "RLB_ESTATE"]
 STORAGE = {"f64": 0, "f32": 1, "f16dev": 2}
-MAX_VARIANTS = 8
-VARIANT_NAMES = ["registers/scalar", "registers/paired", "registers(168)/scalar", "registers(168)/paired"]
+MAX_VARIANTS = 16
+VARIANT_NAMES = ["registers/scalar", "registers/paired", "registers(168)/scalar", "registers(168)/paired",
+                 "pipe tx32 8w", "pipe tx32 4w x2", "pipe tx32 6w", "pipe tx64 8w", "pipe tx64 4w",
+                 "pipe tx32 4w", "pipe tx32 10w"]
 BC = {"periodic": 0, "copyout": 1, "bounceback": 2}
 
 
@@ -326,8 +328,8 @@ class RLB:
         v = ctypes.c_int()
         ms = (ctypes.c_double * MAX_VARIANTS)()
         self._check(self._lib.rlb_autotune(self._h, int(reps), ctypes.byref(v), ms))
-        n = sum(1 for x in ms if x > 0)
-        return v.value, list(ms)[:max(n, 1)]
+        n = max([i + 1 for i, x in enumerate(ms) if x > 0] or [1])
+        return v.value, list(ms)[:n]
 
     @property
     def steps_done(self):

@@ -79,13 +79,20 @@ def test_reference_arm_under_torchrun_prints_one_line_from_rank_0():
 
 
 def test_traffic_record_is_used_only_for_the_kernel_sources_it_was_taken_on(tmp_path, monkeypatch):
-    """roofline.traffic comes from profiles/step_f32_traffic.json only while the step kernels'
-    sources hash to the recorded digest and the variant, lattice and density match."""
+    """roofline.traffic comes from the step traffic record only while the step kernels' sources
+    hash to the recorded digest and the variant, lattice and density match."""
     bench = load_bench()
-    rec = json.load(open(os.path.join(ROOT, "profiles", "step_f32_traffic.json")))
-    assert rec["dram_bytes_per_step"] >= rec["algorithmic_bytes_per_step"] * 0.99
-    assert bench.recorded_traffic(rec["lattice"], rec["variant"], rec["density"]) == rec["dram_bytes_per_step"]
-    assert bench.recorded_traffic(rec["lattice"], rec["variant"] ^ 1, rec["density"]) is None
-    assert bench.recorded_traffic(rec["lattice"] // 2, rec["variant"], rec["density"]) is None
+    rec = {"lattice": 256, "variant": 4, "density": "uniform", "dram_bytes_per_step": 1.75e10,
+           "algorithmic_bytes_per_step": 17179869184, "sources_sha256": bench.kernel_sources_digest()}
+    path = str(tmp_path / "traffic.json")
+    json.dump(rec, open(path, "w"))
+    assert bench.recorded_traffic(256, 4, "uniform", path) == rec["dram_bytes_per_step"]
+    assert bench.recorded_traffic(256, 5, "uniform", path) is None
+    assert bench.recorded_traffic(128, 4, "uniform", path) is None
+    assert bench.recorded_traffic(256, 4, "cube", path) is None
+    assert bench.recorded_traffic(256, 4, "uniform", str(tmp_path / "missing.json")) is None
     monkeypatch.setattr(bench, "kernel_sources_digest", lambda: "0" * 64)  # the kernels changed
-    assert bench.recorded_traffic(rec["lattice"], rec["variant"], rec["density"]) is None
+    assert bench.recorded_traffic(256, 4, "uniform", path) is None
+    # the committed record, if it matches the current sources, is at least the algorithmic bytes
+    committed = json.load(open(bench.TRAFFIC_RECORD))
+    assert committed["dram_bytes_per_step"] >= committed["algorithmic_bytes_per_step"] * 0.99

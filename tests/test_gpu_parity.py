@@ -231,7 +231,8 @@ def test_autotune_keeps_the_state_and_picks_a_variant():
         a.init(n, T, u)
         b.init(n, T, u)
         v, ms = a.autotune(reps=2)
-        assert 0 <= v < len(ms) and len(ms) == 4 and all(t > 0 for t in ms)
+        # register variants 0..3 and the pipelined shapes that fit this lattice
+        assert 0 <= v < len(ms) and len(ms) >= 5 and ms[v] > 0 and all(t > 0 for t in ms[:5])
         assert np.array_equal(a.populations(), b.populations())  # autotuning changed nothing
         a.step(1)
         with pytest.raises(RLBError) as e:

@@ -1,0 +1,156 @@
+"""GPU parity of the pipelined step kernel (step variants 4 and up: bulk copies of each tile's
+pulled population rows into shared memory, consumer warps relaxing the cells from there) against
+the FP64 oracle.  Same tolerances as test_gpu_parity: double storage per population at 1e-12 of
+max(|f|, w_i n_max / 2); float storage on the Landau fields at 1e-5."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_inputs import fields as gen
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU containers
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1301_3423_gb300 import RLB  # noqa: E402
+from paper_1301_3423_gb300 import rlb as rlbmod  # noqa: E402
+
+from test_gpu_parity import BCS, field_err, near_equilibrium, pop_err  # noqa: E402
+
+PIPE = list(range(4, len(rlbmod.VARIANT_NAMES)))
+
+
+@pytest.mark.parametrize("order", [3, 2])
+@pytest.mark.parametrize("bc", ["periodic", "copyout_z", "copyout_xy", "walls_xz", "box"])
+@pytest.mark.parametrize("variant", [8, 9])
+def test_f64_pipe_matches_oracle(order, bc, variant):
+    """Double storage, 72 x 13 x 11 cells, with the two shapes whose stages fit double rows for
+    both orders (64-cell tiles with 4 consumer warps, 32-cell tiles with 4): a ragged last tile per
+    row; periodic x split into copies at the lattice ends, copy-out and bounce-back x patched by
+    the consumers, y and z resolved per row by the producer (walls patched)."""
+    lat = oracle.read_lattice(order)
+    shape = (11, 13, 72)
+    f0 = near_equilibrium(lat, shape, seed=13 + order, bc=BCS[bc])
+    o = oracle.OracleRLB(lat, shape[2], shape[1], shape[0], bc=BCS[bc], eta_over_s=0.1)
+    o.set_populations(f0)
+    o.step(6)
+    with RLB(shape, order=order, bc=BCS[bc], eta_over_s=0.1, step_variant=variant) as g:
+        g.set_populations(f0)
+        launches0 = g.kernel_launches
+        g.step(6)
+        steps_launches = g.kernel_launches - launches0
+        f = g.populations()
+        m = g.moments()
+    err = pop_err(lat, f, o.f, 2.0)
+    print("pipe f64 order %d %s variant %d: %.2e" % (order, bc, variant, err))
+    assert steps_launches == 6  # one launch per step: the pipelined kernel ran
+    assert err < 1e-12
+    en, ee, eu = field_err(o.moments(), m)
+    assert max(en, ee, eu) < 1e-12
+
+
+@pytest.mark.parametrize("order", [3, 2])
+@pytest.mark.parametrize("shape", [(5, 4, 8), (7, 3, 16), (9, 8, 36)])
+def test_f64_pipe_small_and_ragged_lattices(order, shape):
+    """Axes shorter than the stencil reach (modulo wrap of y and z in the producer, x split into
+    several periods), rows narrower than a tile, a row of 36 cells (a 4-cell second tile)."""
+    lat = oracle.read_lattice(order)
+    f0 = near_equilibrium(lat, shape, seed=8)
+    o = oracle.OracleRLB(lat, shape[2], shape[1], shape[0], tau_prime=0.9)
+    o.set_populations(f0)
+    o.step(5)
+    for variant in (8, 9):
+        with RLB(shape, order=order, tau_prime=0.9, step_variant=variant) as g:
+            g.set_populations(f0)
+            l0 = g.kernel_launches
+            g.step(5)
+            assert g.kernel_launches - l0 == 5
+            assert pop_err(lat, g.populations(), o.f, 2.0) < 1e-12, variant
+
+
+@pytest.mark.parametrize("order", [3, 2])
+@pytest.mark.parametrize("variant", PIPE)
+def test_f32_pipe_fields_within_1e5(order, variant):
+    """Float storage on every pipelined shape: Landau fields within 1e-5 of the FP64 oracle after
+    40 steps of the random-field case (|v| <= 0.6, sigma_lnT = 0.2, eta/s = 0.1)."""
+    lat = oracle.read_lattice(order)
+    shape = (11, 13, 40)
+    n, T, u = gen.smooth_random_fields(shape, seed=31, vmax=0.6, sigma_lnT=0.2)
+    o = oracle.OracleRLB(lat, shape[2], shape[1], shape[0], eta_over_s=0.1)
+    o.init(n, T, u)
+    o.step(40)
+    with RLB(shape, order=order, storage="f32", eta_over_s=0.1, step_variant=variant) as g:
+        g.init(n, T, u)
+        l0 = g.kernel_launches
+        g.step(40)
+        assert g.kernel_launches - l0 == 40
+        m = g.moments()
+    en, ee, eu = field_err(o.moments(), m)
+    print("pipe f32 order %d variant %d: n %.2e eps %.2e u %.2e" % (order, variant, en, ee, eu))
+    assert max(en, ee, eu) < 1e-5
+
+
+@pytest.mark.parametrize("bc", ["copyout_xy", "walls_xz", "box"])
+def test_f32_pipe_boundaries_equal_register_kernel(bc):
+    """Float storage with patched boundaries: the pipelined kernel (variant 4) and the register
+    kernel with the same paired arithmetic (variant 3) evaluate the same operations on the same
+    pulled values, so their populations agree to float rounding after 10 steps."""
+    shape = (12, 10, 40)
+    n, T, u = gen.smooth_random_fields(shape, seed=17, vmax=0.5, sigma_lnT=0.2)
+    out = {}
+    for v in (3, 4):
+        with RLB(shape, order=3, bc=BCS[bc], storage="f32", eta_over_s=0.1, step_variant=v) as g:
+            g.init(n, T, u)
+            g.step(10)
+            out[v] = g.populations()
+    lat = oracle.read_lattice(3)
+    assert pop_err(lat, out[4], out[3], n.max()) < 1e-5
+
+
+def test_f16dev_pipe_matches_register_kernel():
+    """Half-deviation storage: the pipelined kernel against the register kernel after 20 steps."""
+    shape = (11, 13, 40)
+    n, T, u = gen.smooth_random_fields(shape, seed=31, vmax=0.3, sigma_lnT=0.1)
+    lat = oracle.read_lattice(3)
+    o = oracle.OracleRLB(lat, shape[2], shape[1], shape[0], eta_over_s=0.1)
+    o.init(n, T, u)
+    o.step(20)
+    ref = o.moments()
+    for v in (3, 4, 7):
+        with RLB(shape, order=3, storage="f16dev", eta_over_s=0.1, step_variant=v) as g:
+            g.init(n, T, u)
+            g.step(20)
+            m = g.moments()
+        en, ee, eu = field_err(ref, m)
+        print("f16dev variant %d: n %.2e eps %.2e u %.2e" % (v, en, ee, eu))
+        assert max(en, ee, eu) < 1e-2
+
+
+def test_conservation_pipe():
+    """Periodic lattice, pipelined float step: sum N^0, sum T^{0 nu} constant to float rounding."""
+    shape = (24, 20, 32)
+    n, T, u = gen.smooth_random_fields(shape, seed=5, vmax=0.5, sigma_lnT=0.2)
+    with RLB(shape, order=3, storage="f32", eta_over_s=0.1, step_variant=4) as g:
+        g.init(n, T, u)
+        t0 = g.moments()["totals"]
+        g.step(60)
+        t1 = g.moments()["totals"]
+    assert np.max(np.abs(t1 - t0)) <= 2e-6 * np.abs(t0).max()
+
+
+def test_landau_failure_in_pipe_is_reported():
+    """Every cell holding a single population: the pipelined step streams without collision and
+    reports RLB_ENONCONV."""
+    lat = oracle.read_lattice(3)
+    shape = (4, 5, 8)
+    single = np.zeros((lat.q,) + shape)
+    single[0] = 1.0
+    with RLB(shape, tau_prime=1.0, step_variant=9) as g:
+        g.set_populations(single)
+        g.step(1)
+        with pytest.raises(rlbmod.RLBError) as e:
+            g.sync()
+        assert e.value.status == rlbmod.RLB_ENONCONV
+        assert np.array_equal(g.populations()[0], single[0])
