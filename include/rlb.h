@@ -220,6 +220,10 @@ const char* rlb_batch_last_error(const rlb_batch* b);
 /* Release the batch (not its members' contexts).  Synchronises its stream.  NULL is accepted. */
 rlb_status rlb_batch_destroy(rlb_batch* b);
 
+/* The step-kernel variant rlb_step uses (see rlb_autotune; -1 for NULL): the one rlb_params asked
+ * for if it exists for this context, else the library default, or the autotuner's choice. */
+int rlb_step_variant(const rlb_ctx* ctx);
+
 /* Number of time steps taken since rlb_init / rlb_set_populations (-1 for NULL). */
 long rlb_steps_done(const rlb_ctx* ctx);
 

@@ -25,7 +25,7 @@ INSTANCES = [(o, s) for o in (3, 2) for s in (0, 1, 2)]
 # step-kernel variants compiled per (order, storage): one for double storage, four for float ones
 VARIANT_UNITS = [(o, s, v) for o, s in INSTANCES for v in ((0,) if s == 0 else (0, 1, 2, 3))]
 # pipelined step kernel per (order, storage) and tile width
-PIPE_UNITS = [(o, s, tx) for o, s in INSTANCES for tx in (32, 64)]
+PIPE_UNITS = [(o, s, tx) for o, s in INSTANCES for tx in (64, 128)]
 
 
 def _nvcc():

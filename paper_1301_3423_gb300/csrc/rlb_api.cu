@@ -168,9 +168,16 @@ static bool pipe_shape(const rlb_ctx* c, int v, PipeParams* pp, int* grid, int* 
   if (c->sp.nx % A != 0 || c->sms <= 0) return false;
   const long long stage = (long long)c->q * (cf.tx + A) * (long long)c->elem;
   const long long budget = std::min<long long>(c->smem_optin, c->smem_per_sm / cf.ctas_per_sm - 1024);
-  const int nstage = (int)std::min<long long>(kPipeMaxStages, (budget - kPipeHeaderBytes) / stage);
-  const int groups = cf.cons_warps / (cf.tx / 32);
-  if (groups < 1 || nstage < groups + 1) return false;
+  // float storage splits each cell between a pair of consumer warps
+  const bool split = c->elem == 4;
+  const int wpt = cf.tx / 32 * (split ? 2 : 1);
+  const int groups = cf.cons_warps / wpt;
+  if (groups < 1 || cf.cons_warps % wpt != 0 || cf.producers < 1) return false;
+  const long long xchg = split ? (long long)cf.cons_warps / 2 * kPipeXchgBytesPerPair : 0;
+  // stages: the largest multiple of the group count that fits, at least two per group
+  const int fit = (int)std::min<long long>(kPipeMaxStages, (budget - kPipeHeaderBytes - xchg) / stage);
+  const int nstage = fit / groups * groups;
+  if (nstage < 2 * groups || cf.producers > c->q) return false;
   PipeParams r{};
   r.segs = (c->sp.nx + cf.tx - 1) / cf.tx;
   const long long ntiles = (long long)r.segs * c->sp.ny * c->sp.nz;
@@ -179,10 +186,14 @@ static bool pipe_shape(const rlb_ctx* c, int v, PipeParams* pp, int* grid, int* 
   r.nstage = nstage;
   r.groups = groups;
   r.xperiodic = c->sp.bc[0] == kPeriodic ? 1 : 0;
+  r.producers = cf.producers;
+  if (cf.producers > kPipeMaxProducerWarps || cf.cons_warps > kPipeMaxConsumerWarps ||
+      cf.cons_warps + cf.producers > kPipeMaxWarps)
+    return false;
   if (pp) *pp = r;
   if (grid) *grid = (int)std::min<long long>((long long)c->sms * cf.ctas_per_sm, ntiles);
-  if (threads) *threads = (cf.cons_warps + 1) * 32;
-  if (smem) *smem = (int)(kPipeHeaderBytes + nstage * stage);
+  if (threads) *threads = (cf.cons_warps + cf.producers) * 32;
+  if (smem) *smem = (int)(kPipeHeaderBytes + nstage * stage + xchg);
   return true;
 }
 
@@ -332,6 +343,7 @@ extern "C" rlb_status rlb_destroy(rlb_ctx* c) {
 
 extern "C" const char* rlb_last_error(const rlb_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
 extern "C" long rlb_steps_done(const rlb_ctx* c) { return c ? c->steps : -1; }
+extern "C" int rlb_step_variant(const rlb_ctx* c) { return c ? c->variant : -1; }
 extern "C" long rlb_kernel_launches(const rlb_ctx* c) { return c ? c->launches : -1; }
 
 static rlb_status check_launch(rlb_ctx* c, cudaError_t e, const char* what) {

@@ -14,21 +14,29 @@ constexpr int kDefaultStepVariant = 0;  // step-kernel variant before autotuning
 // rows start on 16-byte boundaries.
 constexpr int kNumRegVariants = 4;
 struct PipeConfig {
-  int tx;           // tile width in cells (32 or 64; TX / 32 consumer warps per tile)
-  int cons_warps;   // consumer warps per block
+  int tx;           // tile width in cells (64 or 128)
+  int cons_warps;   // consumer warps per block: TX / 32 per tile, twice that with float storage
+                    // (two warps per cell); a multiple of the warps per tile
   int ctas_per_sm;  // resident blocks per SM (the shared memory is split between them)
+  int producers;    // producer warps per block (each copies every producers-th population of every tile)
 };
-constexpr PipeConfig kPipeConfigs[] = {{32, 8, 1}, {32, 4, 2}, {32, 6, 1}, {64, 8, 1},
-                                       {64, 4, 1}, {32, 4, 1}, {32, 10, 1}};
+// A block's stage count is a multiple of its consumer-group count, so that every stage is read by
+// one consumer group, in the order of the stage's uses like every producer: a parity wait then
+// always refers to the phase it means.
+constexpr PipeConfig kPipeConfigs[] = {{128, 8, 1, 8}, {128, 8, 1, 4}, {64, 8, 1, 8}, {64, 4, 1, 4},
+                                       {128, 8, 1, 6}, {64, 8, 1, 4}, {128, 4, 1, 4}, {64, 2, 1, 4}};
 constexpr int kNumPipeConfigs = sizeof(kPipeConfigs) / sizeof(kPipeConfigs[0]);
 constexpr int kNumVariantsTotal = kNumRegVariants + kNumPipeConfigs;
 constexpr int kPipeMaxStages = 16;
-constexpr int kPipeMaxConsumerWarps = 12;  // launch bound of k_step_pipe
+constexpr int kPipeMaxConsumerWarps = 12;
+constexpr int kPipeMaxProducerWarps = 12;
+constexpr int kPipeMaxWarps = 16;  // consumers + producers: the launch bound of k_step_pipe (128 registers)
 constexpr int kPipeHeaderBytes = 1024;  // mbarriers (2 x 16 x 8 B) and the per-population velocity table
+constexpr int kPipeXchgBytesPerPair = 2 * 2 * 13 * 32 * 4;  // partial moments a consumer warp pair exchanges
 // Bytes of slack before and after every population buffer: the pipelined kernel's copies of a row
 // segment next to a lattice end may start up to one granule before the row and end up to one tile
-// plus the stencil reach after it.
-constexpr int kPopGuardBytes = 1024;
+// plus a granule plus the stencil reach after it ((128 + 2 + 6) doubles = 1088 bytes at most).
+constexpr int kPopGuardBytes = 2048;
 
 // ---------------------------------------------------------------------------------------------
 // launch parameters
@@ -69,6 +77,7 @@ enum : int { kStatusNonconv = 0, kStatusBadInit = 1, kStatusTimeout = 2, kStatus
 // Launch shape of a pipelined step (k_step_pipe): tiles are TX-cell segments of the lattice rows,
 // tile t = row * segs + seg, block b takes tiles b, b + grid, ...
 struct PipeParams {
+  int producers;  // producer warps per block
   int ntiles;     // segs * ny * nz
   int segs;       // tiles per row, ceil(nx / TX)
   int nstage;     // shared-memory stages per block (<= 16)

@@ -75,8 +75,8 @@ cudaError_t convert_pops(void* pop, double* dbl, int i0, int i1, bool to_f64, co
 
 cudaError_t pipe_step(const void* src, void* dst, const StepParams& p, const PipeParams& pp, int* status, int tx,
                       int grid, int threads, int smem, cudaStream_t s) {
-  if (tx == 64) return RLB_PFN(pipe, 64)(src, dst, p, pp, status, grid, threads, smem, s);
-  return RLB_PFN(pipe, 32)(src, dst, p, pp, status, grid, threads, smem, s);
+  if (tx == 128) return RLB_PFN(pipe, 128)(src, dst, p, pp, status, grid, threads, smem, s);
+  return RLB_PFN(pipe, 64)(src, dst, p, pp, status, grid, threads, smem, s);
 }
 
 }  // namespace

@@ -47,8 +47,8 @@ constexpr int kVariants = kFloat ? kNumVariants : 1;
 #define RLB_DECLARE_PIPE(tx)                                                                                   \
   cudaError_t RLB_PFN(pipe, tx)(const void* src, void* dst, const StepParams& p, const PipeParams& pp, int* status, \
                                 int grid, int threads, int smem, cudaStream_t s);
-RLB_DECLARE_PIPE(32)
 RLB_DECLARE_PIPE(64)
+RLB_DECLARE_PIPE(128)
 #undef RLB_DECLARE_PIPE
 
 RLB_DECLARE_VARIANT(0)

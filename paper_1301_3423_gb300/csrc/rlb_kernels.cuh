@@ -543,12 +543,14 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
-template <class L, bool DEV = false, class Get2>
-__device__ __forceinline__ Mom<float> moments_f2(Get2&& get2, float c = 0.f) {
+// Sums of the direction pairs [DPB, DPE) in paired arithmetic: the 13 independent moments before
+// the weights' own moments (deviation space) and the trace identity are added (finish_moments_f2).
+template <class L, bool DEV = false, int DPB = 0, int DPE = L::NDP, class Get2>
+__device__ __forceinline__ Mom<float> moments_f2_part(Get2&& get2) {
   const float2 z = f2(0.f, 0.f);
   float2 N0 = z, Nx = z, Ny = z, Nz = z, T00 = z, T0x = z, T0y = z, T0z = z, Txx = z, Tyy = z, Txy = z, Txz = z, Tyz = z;
-  static_for<L::NDP>([&](auto K) {
-    constexpr int k = decltype(K)::value;
+  static_for<DPE - DPB>([&](auto K) {
+    constexpr int k = DPB + decltype(K)::value;
     constexpr int first = L::DP_FIRST[k];
     constexpr int np = L::DP_NPAIR[k];
     float2 S1 = z, S2 = z;  // (sum over energies for +v, for -v)
@@ -611,20 +613,45 @@ __device__ __forceinline__ Mom<float> moments_f2(Get2&& get2, float c = 0.f) {
   m.Txy = Txy.x + Txy.y;
   m.Txz = Txz.x + Txz.y;
   m.Tyz = Tyz.x + Tyz.y;
-  if constexpr (DEV) add_rest_sums<L, float>(m, c);
-  m.Tzz = m.T00 - m.Txx - m.Tyy;
+  m.Tzz = 0.f;
   return m;
 }
 
-template <class L, bool DEV = false, class Get2, class Put2>
+// The weights' own moments times c (deviation space) and T^zz from the trace identity.
+template <class L, bool DEV = false>
+__device__ __forceinline__ void finish_moments_f2(Mom<float>& m, float c = 0.f) {
+  if constexpr (DEV) add_rest_sums<L, float>(m, c);
+  m.Tzz = m.T00 - m.Txx - m.Tyy;
+}
+
+template <class L, bool DEV = false, class Get2>
+__device__ __forceinline__ Mom<float> moments_f2(Get2&& get2, float c = 0.f) {
+  Mom<float> m = moments_f2_part<L, DEV>(get2);
+  finish_moments_f2<L, DEV>(m, c);
+  return m;
+}
+
+// Collision of the direction pairs [DPB, DPE) (all of them by default).
+template <class L, bool DEV = false, int DPB = 0, int DPE = L::NDP, class Get2, class Put2>
 __device__ __forceinline__ void collide_f2(const Landau<float>& lw, float T, float inv_tau, Get2&& get2, Put2&& put2,
                                            float c = 0.f) {
-  const LevCoef<L, float> e = level_coef<L, float>(eq_coef<L::ORDER, float>(lw.n, T, lw.U0), DEV ? c : 0.f);
+  const LevCoef<L, float> e1 = level_coef<L, float>(eq_coef<L::ORDER, float>(lw.n, T, lw.U0), DEV ? c : 0.f);
+  // the coefficients as (x, x) pairs once per cell, the operands of the paired Horner steps
+  struct {
+    float2 a[L::NLEV], b[L::NLEV], c[L::NLEV], d[L::NLEV];
+  } e;
+  static_for<L::NLEV>([&](auto K) {
+    constexpr int l = decltype(K)::value;
+    e.a[l] = f2(e1.a[l], e1.a[l]);
+    e.b[l] = f2(e1.b[l], e1.b[l]);
+    e.c[l] = f2(e1.c[l], e1.c[l]);
+    e.d[l] = f2(e1.d[l], e1.d[l]);
+  });
   const float a = lw.U0 * inv_tau;
   const float2 Uxp = f2(lw.Ux, lw.Ux), Uyp = f2(lw.Uy, lw.Uy), Uzp = f2(lw.Uz, lw.Uz);
   const float2 itp = f2(inv_tau, inv_tau), nap = f2(-a, -a);
-  static_for<L::NDP>([&](auto K) {
-    constexpr int k = decltype(K)::value;
+  static_for<DPE - DPB>([&](auto K) {
+    constexpr int k = DPB + decltype(K)::value;
     constexpr int first = L::DP_FIRST[k];
     constexpr int np = L::DP_NPAIR[k];
     constexpr int vx = L::VX[first], vy = L::VY[first], vz = L::VZ[first];
@@ -640,10 +667,9 @@ __device__ __forceinline__ void collide_f2(const Landau<float>& lw, float T, flo
       constexpr float nw = DEV ? -1.f : (float)(-L::W[ip]);
       float2 E;
       if constexpr (L::ORDER == 3)
-        E = ffma2(tt, ffma2(tt, ffma2(tt, f2(e.d[l], e.d[l]), f2(e.c[l], e.c[l])), f2(e.b[l], e.b[l])),
-                  f2(e.a[l], e.a[l]));
+        E = ffma2(tt, ffma2(tt, ffma2(tt, e.d[l], e.c[l]), e.b[l]), e.a[l]);
       else
-        E = ffma2(tt, ffma2(tt, f2(e.c[l], e.c[l]), f2(e.b[l], e.b[l])), f2(e.a[l], e.a[l]));
+        E = ffma2(tt, ffma2(tt, e.c[l], e.b[l]), e.a[l]);
       const float2 f = get2(ic<ip>{});
       const float2 d = ffma2(f2(nw, nw), E, f);  // f - w E (deviation space: d - (E - c))
       put2(ic<ip>{}, ffma2(nom, d, f));        // f - omega (f - w E)

@@ -2,7 +2,7 @@
 // (TMA) engine, with warp-specialised producer and consumer warps (sm_90+ PTX: mbarrier,
 // cp.async.bulk).
 //
-// A tile is one 32- or 64-cell segment of a lattice row (fixed y, z; x0 a multiple of the tile
+// A tile is one 64- or 128-cell segment of a lattice row (fixed y, z; x0 a multiple of the tile
 // width TX).  For every population i the cells x0 .. x0 + TX - 1 pull from the row
 // (y - vy_i, z - vz_i) at x - vx_i, i.e. from one contiguous run of the source plane.  The
 // producer warp copies that run, widened to 16-byte boundaries, into the tile's stage with one
@@ -20,8 +20,12 @@
 // by one producer lane per population instead of 32 lanes each computing an address.
 //
 // Stages form a ring of NSTAGE slots per block: tile k of a block goes to stage k % NSTAGE and to
-// consumer group k % groups.  full[s] completes when the copies of the stage's tile have landed;
-// empty[s] when every consumer warp of that tile has finished reading it.  Every wait is bounded
+// consumer group k % groups; every producer warp copies its share of the populations of every
+// tile.  NSTAGE is a multiple of the group count, so each stage is read by one group, and every
+// producer and that group take the stage's uses in order: when either waits for use u of a stage,
+// use u - 1 is complete and use u + 1 cannot be, and the parity of u names the right phase.
+// full[s] completes when every producer has arrived for the stage's tile and its copies have
+// landed; empty[s] when every consumer warp of that tile has finished reading it.  Every wait is bounded
 // (kPipeWaitNs); a wait that runs out counts in status[kStatusTimeout], and the producer then waits
 // (bounded) for the copies it has in flight before it returns.
 #pragma once
@@ -32,7 +36,7 @@
 
 namespace rlb {
 
-constexpr int kPipeMaxThreads = (kPipeMaxConsumerWarps + 1) * 32;
+constexpr int kPipeMaxThreads = kPipeMaxWarps * 32;
 constexpr unsigned long long kPipeWaitNs = 2000000000ull;  // 2 s
 
 // Geometry of one staged row for storage S and tile width TX.
@@ -104,12 +108,70 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 // Orders this thread's generic-proxy shared-memory writes before later bulk copies into them.
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// Named barrier over `threads` threads (a multiple of 32).
+__device__ __forceinline__ void named_barrier(int id, int threads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// The direction pair at which the populations split into two halves of (nearly) equal size.
+template <class L>
+struct DpSplit {
+  static constexpr int find() {
+    int acc = 0;
+    for (int k = 0; k < L::NDP; ++k) {
+      acc += 2 * L::DP_NPAIR[k];
+      if (2 * acc >= L::Q) return k + 1;
+    }
+    return L::NDP;
+  }
+  static constexpr int value = find();
+};
+
+// Floats a consumer warp pair exchanges per tile: two buffers (alternate tiles) x two halves x 13
+// partial moments x 32 lanes.
+constexpr int kPipeXchgFloatsPerPair = kPipeXchgBytesPerPair / 4;
+
+// Publish this warp's 13 partial moments (T^zz follows from the trace later), wait for the partner
+// warp at named barrier `id`, and add the partner's.  Both warps add the same two numbers, so they
+// hold identical moments.  The buffers alternate between tiles: a warp writes a buffer again only
+// after the partner has passed the next barrier, i.e. after it has read that buffer.
+__device__ __forceinline__ void exchange_moments(Mom<float>& m, float* mine, const float* other, int id) {
+  mine[0 * 32] = m.N0;
+  mine[1 * 32] = m.Nx;
+  mine[2 * 32] = m.Ny;
+  mine[3 * 32] = m.Nz;
+  mine[4 * 32] = m.T00;
+  mine[5 * 32] = m.T0x;
+  mine[6 * 32] = m.T0y;
+  mine[7 * 32] = m.T0z;
+  mine[8 * 32] = m.Txx;
+  mine[9 * 32] = m.Tyy;
+  mine[10 * 32] = m.Txy;
+  mine[11 * 32] = m.Txz;
+  mine[12 * 32] = m.Tyz;
+  named_barrier(id, 64);
+  m.N0 += other[0 * 32];
+  m.Nx += other[1 * 32];
+  m.Ny += other[2 * 32];
+  m.Nz += other[3 * 32];
+  m.T00 += other[4 * 32];
+  m.T0x += other[5 * 32];
+  m.T0y += other[6 * 32];
+  m.T0z += other[7 * 32];
+  m.Txx += other[8 * 32];
+  m.Tyy += other[9 * 32];
+  m.Txy += other[10 * 32];
+  m.Txz += other[11 * 32];
+  m.Tyz += other[12 * 32];
+}
+
 // -------------------------------------------------------------------------------------------------
 // the kernel
 // -------------------------------------------------------------------------------------------------
 // Source row of a pull along y or z: periodic wrap (any length) or copy-out clamp.  Beyond a
 // bounce-back wall any in-range row will do: the consumer replaces those populations.
 __device__ __forceinline__ int pipe_src_row(int s, int n, int bc) {
+  if ((unsigned)s < (unsigned)n) return s;
   if (bc == kPeriodic) {
     s %= n;
     return s < 0 ? s + n : s;
@@ -125,9 +187,14 @@ __global__ void __launch_bounds__(kPipeMaxThreads, 1)
   using T = typename S::T;
   using A = typename S::A;
   using Sh = PipeShape<S, TX>;
-  constexpr int BX = Sh::BX, AL = Sh::A, WPT = TX / 32;
-  constexpr int kStageElems = L::Q * BX;
   constexpr bool PACKED = std::is_same<A, float>::value;
+  // float storage: two warps per cell (see the consumer section); half storage, whose stages are
+  // half the size, runs more consumer groups instead
+  constexpr bool SPLIT = std::is_same<S, StoreF32>::value;
+  constexpr int HALVES = SPLIT ? 2 : 1;
+  constexpr int KS = SPLIT ? DpSplit<L>::value : L::NDP;
+  constexpr int BX = Sh::BX, AL = Sh::A, WPT = TX / 32 * HALVES;
+  constexpr int kStageElems = L::Q * BX;
   constexpr bool DEV = std::is_same<S, StoreF16Dev>::value;
   static_assert(TX % 32 == 0 && TX >= 32, "tile width");
 
@@ -138,10 +205,10 @@ __global__ void __launch_bounds__(kPipeMaxThreads, 1)
   T* const stage0 = reinterpret_cast<T*>(smem + kPipeHeaderBytes);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int cons_warps = pp.groups * WPT;
+  const int cons_warps = pp.groups * WPT;  // warps [0, cons_warps) consume, the next pp.producers produce
   if (threadIdx.x == 0) {
     for (int s = 0; s < pp.nstage; ++s) {
-      mbar_init(&full[s], 1);
+      mbar_init(&full[s], pp.producers);
       mbar_init(&empty[s], WPT);
     }
     static_for<L::Q>([&](auto I) {
@@ -154,8 +221,13 @@ __global__ void __launch_bounds__(kPipeMaxThreads, 1)
   __syncthreads();
   const long long G = gridDim.x;
 
-  if (warp == cons_warps) {
-    // ---- producer warp: one bulk copy (or a few, at a periodic x end) per population and tile
+  if (warp >= cons_warps) {
+    // ---- producer warps, a team over every tile: producer w copies populations i = w, w + P, ...
+    // (lane l takes i = l P + w, then i + 32 P), one bulk copy each (a few at a periodic x end),
+    // and arrives once per tile on the stage's full barrier with its share of the bytes
+    const int pw = warp - cons_warps;
+    const int P = pp.producers;
+    const int mine = (L::Q - pw + P - 1) / P;  // populations of this producer
     int k = 0;
     bool ok = true;
     for (;; ++k) {
@@ -166,20 +238,20 @@ __global__ void __launch_bounds__(kPipeMaxThreads, 1)
         ok = false;
         break;
       }
-      if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)(kStageElems * sizeof(T)));
+      if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)(mine * Sh::ROW_BYTES));
       __syncwarp();
       const int seg = (int)(t % pp.segs), row = (int)(t / pp.segs);
       const int y = row % p.ny, z = row / p.ny;
       const int x0 = seg * TX;
       T* const st = stage0 + (size_t)s * kStageElems;
-      for (int i = lane; i < L::Q; i += 32) {
+      for (int i = lane * P + pw; i < L::Q; i += 32 * P) {
         const char4 v = sv[i];
         const int ys = pipe_src_row(y - v.y, p.ny, p.bc[1]);
         const int zs = pipe_src_row(z - v.z, p.nz, p.bc[2]);
         const T* rowp = src + (long long)i * p.cells + ((long long)zs * p.ny + ys) * p.nx;
         const int xs = (x0 - v.x) & ~(AL - 1);  // round down to a granule (two's complement: floor)
         T* d = st + i * BX;
-        if (pp.xperiodic) {
+        if (pp.xperiodic && (xs < 0 || xs + BX > p.nx)) {
           // split [xs, xs + BX) at multiples of nx; each piece is whole granules of one period
           int a = xs;
           const int e = xs + BX;
@@ -198,16 +270,25 @@ __global__ void __launch_bounds__(kPipeMaxThreads, 1)
     }
     if (!ok) {
       if (lane == 0) atomicAdd(&status[kStatusTimeout], 1);
-      // let the copies already issued land before the block's shared memory goes away
+      // let the copies already issued land before the block's shared memory goes away (each stage's
+      // latest use among the last nstage tiles)
       for (int j = max(0, k - pp.nstage); j < k; ++j) mbar_wait(&full[j % pp.nstage], (uint32_t)(j / pp.nstage) & 1u);
     }
     return;
   }
-  if (warp > cons_warps) return;
-
-  // ---- consumer warps: lane x of part wt of the tile is cell x0 + 32 wt + x
+  // ---- consumer warps.  Float storage splits every cell between two warps of a pair (HALVES =
+  // 2): one takes the direction pairs [0, KS), the other [KS, NDP), each sums its partial moments,
+  // the pair adds them through shared memory (a named barrier per pair and tile), both solve the
+  // same Landau matching and each collides its own half.  Lane x of part `part` of the tile is
+  // cell x0 + 32 part + x.
   const int group = warp / WPT, wt = warp % WPT;
-  for (int k = group;; k += pp.groups) {
+  const int part = wt / HALVES, half = wt % HALVES;
+  float* const xb = SPLIT ? reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(stage0) +
+                                                     (size_t)pp.nstage * kStageElems * sizeof(T)) +
+                                (warp >> 1) * kPipeXchgFloatsPerPair + lane
+                          : nullptr;
+  int iter = 0;
+  for (int k = group;; k += pp.groups, ++iter) {
     const long long t = blockIdx.x + (long long)k * G;
     if (t >= pp.ntiles) break;
     const int s = k % pp.nstage;
@@ -220,13 +301,13 @@ __global__ void __launch_bounds__(kPipeMaxThreads, 1)
     cl.y = row % p.ny;
     cl.z = row / p.ny;
     const int x0 = seg * TX;
-    const int x = x0 + wt * 32 + lane;
+    const int x = x0 + part * 32 + lane;
     const bool valid = x < p.nx;
     cl.x = valid ? x : p.nx - 1;
     cl.c = (cl.z * p.ny + cl.y) * p.nx + cl.x;
-    T* const lb = stage0 + (size_t)s * kStageElems + wt * 32 + lane;
+    T* const lb = stage0 + (size_t)s * kStageElems + part * 32 + lane;
 
-    // patch what the copies could not express (warp-uniform test)
+    // patch what the copies could not express (warp-uniform test), for the populations this warp reads
     bool patch = !pp.xperiodic && (x0 < L::VMAX_X || x0 + TX - 1 + L::VMAX_X >= p.nx);
     if constexpr (WALLS)
       patch = patch || (p.bc[1] == kBounceBack && (cl.y < L::VMAX_Y || cl.y >= p.ny - L::VMAX_Y)) ||
@@ -236,6 +317,8 @@ __global__ void __launch_bounds__(kPipeMaxThreads, 1)
         constexpr int i = decltype(I)::value;
         constexpr int vx = L::VX[i];
         constexpr int r = ((-vx) % AL + AL) % AL;
+        constexpr int ih = i < L::DP_FIRST[KS % L::NDP] || KS == L::NDP ? 0 : 1;  // half of population i
+        if (SPLIT && ih != half) return;
         bool need = false;
         if constexpr (WALLS) need = p.has_wall && beyond_wall<L, i>(cl, p);
         if constexpr (vx != 0) need = need || (!pp.xperiodic && (unsigned)(cl.x - vx) >= (unsigned)p.nx);
@@ -260,7 +343,50 @@ __global__ void __launch_bounds__(kPipeMaxThreads, 1)
         else S::template store<L, i>(out + (long long)i * p.cells, v, p);
       }
     };
-    relax_cell<L, S, PACKED, true>(get, store, p, status, valid);
+    if constexpr (!SPLIT) {
+      relax_cell<L, S, PACKED, true>(get, store, p, status, valid);
+    } else {
+      auto get2 = [&](auto I) -> float2 {
+        constexpr int i = decltype(I)::value;
+        return make_float2(get(ic<i>{}), get(ic<i + 1>{}));
+      };
+      const float c_dev = DEV ? p.half_nref : 0.f;
+      Mom<float> m = half == 0 ? moments_f2_part<L, DEV, 0, KS>(get2) : moments_f2_part<L, DEV, KS, L::NDP>(get2);
+      // exchange the 13 partial sums with the partner warp (buffer iter & 1) and add them
+      float* mine = xb + ((iter & 1) * 2 + half) * 13 * 32;
+      const float* other = xb + ((iter & 1) * 2 + (half ^ 1)) * 13 * 32;
+      exchange_moments(m, mine, other, 1 + (warp >> 1));
+      finish_moments_f2<L, DEV>(m, c_dev);
+      reload_barrier();
+      const Landau<float> lw = landau_step<float>(m, p);
+      if (!lw.ok) {
+        // no Landau frame: counted once per cell, each half streamed without collision
+        if (valid) {
+          if (half == 0) atomicAdd(&status[kStatusNonconv], 1);
+          auto stream_half = [&](auto B, auto E) {
+            static_for<decltype(E)::value - decltype(B)::value>([&](auto K) {
+              constexpr int kk = decltype(B)::value + decltype(K)::value;
+              static_for<2 * L::DP_NPAIR[kk]>([&](auto J) {
+                constexpr int i = L::DP_FIRST[kk] + decltype(J)::value;
+                store(ic<i>{}, get(ic<i>{}));
+              });
+            });
+          };
+          if (half == 0) stream_half(ic<0>{}, ic<KS>{});
+          else stream_half(ic<KS>{}, ic<L::NDP>{});
+        }
+      } else {
+        const float Tl = lw.eps / (3.f * lw.n);
+        const float inv_tau = 1.f / tau_prime<float>(Tl, p);
+        auto put2 = [&](auto I, float2 v) {
+          constexpr int i = decltype(I)::value;
+          store(ic<i>{}, v.x);
+          store(ic<i + 1>{}, v.y);
+        };
+        if (half == 0) collide_f2<L, DEV, 0, KS>(lw, Tl, inv_tau, get2, put2, c_dev);
+        else collide_f2<L, DEV, KS, L::NDP>(lw, Tl, inv_tau, get2, put2, c_dev);
+      }
+    }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
   }

@@ -18,8 +18,8 @@ STATUS_NAMES = ["RLB_OK", "RLB_EINVAL", "RLB_ENOMEM", "RLB_ECUDA", "RLB_ENONCONV
 STORAGE = {"f64": 0, "f32": 1, "f16dev": 2}
 MAX_VARIANTS = 16
 VARIANT_NAMES = ["registers/scalar", "registers/paired", "registers(168)/scalar", "registers(168)/paired",
-                 "pipe tx32 8w", "pipe tx32 4w x2", "pipe tx32 6w", "pipe tx64 8w", "pipe tx64 4w",
-                 "pipe tx32 4w", "pipe tx32 10w"]
+                 "pipe tx128 8c8p", "pipe tx128 8c4p", "pipe tx64 8c8p", "pipe tx64 4c4p", "pipe tx128 8c6p",
+                 "pipe tx64 8c4p", "pipe tx128 4c4p", "pipe tx64 2c4p"]
 BC = {"periodic": 0, "copyout": 1, "bounceback": 2}
 
 
@@ -58,7 +58,7 @@ class Params(ctypes.Structure):
 _LIB = None
 _LOAD_ERROR = None
 DECLARED = ["rlb_default_params", "rlb_bytes_required", "rlb_create", "rlb_init", "rlb_step", "rlb_moments",
-            "rlb_sync", "rlb_get_populations", "rlb_set_populations", "rlb_steps_done", "rlb_kernel_launches",
+            "rlb_sync", "rlb_get_populations", "rlb_set_populations", "rlb_steps_done", "rlb_step_variant", "rlb_kernel_launches",
             "rlb_destroy", "rlb_last_error", "rlb_quadrature", "rlb_autotune", "rlb_totals_noalloc", "rlb_batch_create", "rlb_batch_add",
             "rlb_batch_remove", "rlb_batch_steps_left", "rlb_batch_run", "rlb_batch_autotune",
             "rlb_batch_set_variant", "rlb_batch_kernel_launches", "rlb_batch_last_error", "rlb_batch_destroy"]
@@ -102,6 +102,8 @@ def load(build_if_missing=True):
     lib.rlb_set_populations.restype = ip
     lib.rlb_steps_done.argtypes = [vp]
     lib.rlb_steps_done.restype = ctypes.c_long
+    lib.rlb_step_variant.argtypes = [vp]
+    lib.rlb_step_variant.restype = ip
     lib.rlb_kernel_launches.argtypes = [vp]
     lib.rlb_kernel_launches.restype = ctypes.c_long
     lib.rlb_destroy.argtypes = [vp]
@@ -330,6 +332,11 @@ class RLB:
         self._check(self._lib.rlb_autotune(self._h, int(reps), ctypes.byref(v), ms))
         n = max([i + 1 for i, x in enumerate(ms) if x > 0] or [1])
         return v.value, list(ms)[:n]
+
+    @property
+    def variant(self):
+        """The step-kernel variant rlb_step uses."""
+        return int(self._lib.rlb_step_variant(self._h))
 
     @property
     def steps_done(self):

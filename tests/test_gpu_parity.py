@@ -298,7 +298,9 @@ def test_landau_failure_is_reported_not_hidden():
 @pytest.mark.parametrize("storage,tol,variant,bc", [("f64", 1e-12, -1, "periodic")] +
                          [("f32", 2e-5, v, "periodic") for v in range(4)] +
                          [("f16dev", 2e-2, v, "periodic") for v in (0, 3)] +
-                         [("f64", 1e-12, -1, "box"), ("f32", 2e-5, 3, "box")])
+                         [("f64", 1e-12, -1, "box"), ("f32", 2e-5, 3, "box")] +
+                         [("f32", 2e-5, v, "periodic") for v in (4, 5, 6, 7)] +
+                         [("f64", 1e-12, 11, "periodic"), ("f16dev", 2e-2, 4, "periodic"), ("f32", 2e-5, 4, "box")])
 def test_full_size_sampled_cells(storage, tol, variant, bc):
     """256^3 random-field case in the benchmark's launch configuration: one step from the seeded
     equilibrium, 96 cells (corners, faces, interior, random) against the oracle cell by cell; also
@@ -314,6 +316,7 @@ def test_full_size_sampled_cells(storage, tol, variant, bc):
     o = oracle.OracleRLB(lat, N, N, N, bc=BCS[bc], eta_over_s=0.1)
     ref = o.init_step_cells(n, T, u, sample)
     with RLB(shape, order=3, bc=BCS[bc], storage=storage, eta_over_s=0.1, step_variant=variant) as g:
+        assert variant < 0 or g.variant == variant
         g.init(n, T, u)
         g.step(1)
         dev = torch.empty((lat.q, N ** 3), dtype=torch.float64, device="cuda")
