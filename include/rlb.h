@@ -45,8 +45,8 @@ typedef enum {
   RLB_ENOMEM = 2,   /* device memory could not be allocated */
   RLB_ECUDA = 3,    /* a CUDA call failed; the context should be destroyed */
   RLB_ENONCONV = 4, /* Landau matching found no timelike eigenvector in some cell */
-  RLB_ENAN = 5,     /* non-finite populations were produced */
-  RLB_ETIMEOUT = 6, /* a bounded device-side wait expired */
+  RLB_ENAN = 5,     /* non-finite populations (found by rlb_moments) */
+  RLB_ETIMEOUT = 6, /* a bounded device-side wait of the pipelined step kernel ran out */
   RLB_ESTATE = 7    /* call not valid in the context's current state */
 } rlb_status;
 
@@ -131,11 +131,15 @@ rlb_status rlb_step(rlb_ctx* ctx, long nsteps);
  * double[cells], U double[4][cells] (U^0..U^3), and totals[5] = sum over cells of N^0, T^00,
  * T^0x, T^0y, T^0z (the conserved densities of Eqs. (eq:conser1), (eq:conser2)), summed in double
  * in a fixed order.  Any output pointer may be NULL.  on_device = 1: n, eps, U are device
- * pointers (totals is always host).  Synchronises the stream.  Errors: RLB_ENONCONV (cells without
- * a Landau frame; their fields are NaN), RLB_ENAN, RLB_ECUDA. */
+ * pointers (totals is always host).  Synchronises the stream.  Errors, from this call or from
+ * enqueued work since the last synchronising call: RLB_ENAN (cells whose populations are not
+ * finite), RLB_ENONCONV (cells without a Landau frame, here or in a step; their fields are NaN),
+ * RLB_EINVAL (invalid initial fields given to rlb_init), RLB_ETIMEOUT (a bounded device-side wait
+ * of the pipelined step ran out), RLB_ECUDA. */
 rlb_status rlb_moments(rlb_ctx* ctx, double* n, double* eps, double* U, double totals[5], int on_device);
 
-/* Wait for enqueued work and report deferred errors (as rlb_moments). */
+/* Wait for enqueued work and report deferred errors: RLB_ENONCONV, RLB_EINVAL, RLB_ETIMEOUT,
+ * RLB_ECUDA (as rlb_moments; RLB_ENAN only comes from rlb_moments, which looks at the moments). */
 rlb_status rlb_sync(rlb_ctx* ctx);
 
 /* Copy the stored (post-collision) populations out as double[q][cells].  Synchronises. */
@@ -242,9 +246,10 @@ const char* rlb_last_error(const rlb_ctx* ctx);
 #define RLB_NOALLOC_MAX_CELLS 8388608
 
 /* Conserved totals of a caller-owned population buffer, computed without allocating anything.
- * The paper has no counterpart; this exists for callers that cannot allocate device memory, such
- * as code recording into a stream capture that must not gain allocation nodes, plug-ins whose host
- * owns every allocation, or processes whose memory pools already hold the whole device.
+ * The paper has no counterpart.  It exists for callers that cannot call the device allocator:
+ * plug-ins whose host application owns every device allocation, processes whose memory pools
+ * already hold the whole device, and code that runs under a hard memory budget in which an
+ * allocation by a library would fail or break the budget.
  *
  * f is a device buffer of q * nx * ny * nz populations in the layout and precision of `storage`
  * (the layout of the context buffers: [q][cells], x fastest; RLB_F16DEV stores f_i / w_i - n_ref/2).
@@ -254,10 +259,12 @@ const char* rlb_last_error(const rlb_ctx* ctx);
  *
  * Scratch: a fixed device array inside the library (RLB_NOALLOC_MAX_CELLS / 128 * 5 + 5 doubles,
  * about 2.6 MB) that every device loading the library holds until the process exits.  No
- * cudaMalloc, cudaFree or other allocating routine is called.  The first call on a device looks up
- * that array's device address, with the device current; make that first call before any stream
- * capture.  Every call shares the array: calls whose work overlaps on the GPU (other streams, other
- * host threads) race and must be serialised by the caller.  Nothing in it needs to start at zero.
+ * cudaMalloc, cudaFree or other allocating routine is called ("no allocation" means exactly
+ * that; the call still copies the 5 sums to host memory and synchronises the stream).  The first
+ * call on a device looks up that array's device address, with the device current; make that first
+ * call before any stream capture.  Every call shares the array: calls whose work overlaps on the
+ * GPU (other streams, other host threads) race and must be serialised by the caller.  Nothing in
+ * it needs to start at zero: every slot a call reads, the same call has written.
  *
  * Errors: RLB_EINVAL (order, storage, null pointer, empty lattice, or more than
  * RLB_NOALLOC_MAX_CELLS cells; rlb_last_error(NULL) explains), RLB_ECUDA. */

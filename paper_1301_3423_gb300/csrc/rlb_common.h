@@ -71,8 +71,8 @@ struct StepParams {
 enum : int { kPeriodic = 0, kCopyOut = 1, kBounceBack = 2 };
 
 // status words: cell updates without a Landau frame, cells with invalid initial fields, bounded
-// device-side waits that ran out
-enum : int { kStatusNonconv = 0, kStatusBadInit = 1, kStatusTimeout = 2, kStatusWords = 4 };
+// device-side waits that ran out, cells with non-finite moments (found by the fields kernel)
+enum : int { kStatusNonconv = 0, kStatusBadInit = 1, kStatusTimeout = 2, kStatusNan = 3, kStatusWords = 4 };
 
 // Launch shape of a pipelined step (k_step_pipe): tiles are TX-cell segments of the lattice rows,
 // tile t = row * segs + seg, block b takes tiles b, b + grid, ...

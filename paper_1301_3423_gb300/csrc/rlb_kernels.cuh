@@ -296,7 +296,8 @@ __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
 template <class A>
 struct Landau {
   A U0, Ux, Uy, Uz, eps, n;
-  bool ok;
+  bool ok;    // a timelike frame with eps > 0 and n > 0
+  bool conv;  // the last update moved U by at most tol * U0 (false: stopped at MAXIT)
 };
 
 // Shifted power iteration from the start vector (U0, Ux, Uy, Uz), at most MAXIT updates; a lane
@@ -305,6 +306,7 @@ template <class A, int MAXIT>
 __device__ __forceinline__ Landau<A> landau_from(const Mom<A>& m, A U0, A Ux, A Uy, A Uz, const A tol) {
   Landau<A> r;
   r.ok = false;
+  r.conv = false;
   for (int it = 0; it < MAXIT; ++it) {
     const A V0 = m.T00 * U0 - m.T0x * Ux - m.T0y * Uy - m.T0z * Uz;
     const A Vx = m.T0x * U0 - m.Txx * Ux - m.Txy * Uy - m.Txz * Uz;
@@ -318,7 +320,10 @@ __device__ __forceinline__ Landau<A> landau_from(const Mom<A>& m, A U0, A Ux, A 
     const A n0 = W0 * iw, nx = Wx * iw, ny = Wy * iw, nz = Wz * iw;
     const A d = fmax(fmax(fabs(n0 - U0), fabs(nx - Ux)), fmax(fabs(ny - Uy), fabs(nz - Uz)));
     U0 = n0; Ux = nx; Uy = ny; Uz = nz;
-    if (d <= tol * U0) break;
+    if (d <= tol * U0) {
+      r.conv = true;
+      break;
+    }
   }
   const A V0 = m.T00 * U0 - m.T0x * Ux - m.T0y * Uy - m.T0z * Uz;
   const A Vx = m.T0x * U0 - m.Txx * Ux - m.Txy * Uy - m.Txz * Uz;
@@ -339,6 +344,7 @@ __device__ __forceinline__ Landau<A> landau(const Mom<A>& m) {
   if (!(NN > A(0)) || !(m.N0 > A(0))) {
     Landau<A> r;
     r.ok = false;
+    r.conv = false;
     return r;
   }
   const A is = rsqrt_(NN);
@@ -356,26 +362,40 @@ static __device__ __noinline__ Landau<double> landau_fp64_out_of_line(const Mom<
   if (!(NN > 0.0) || !(m.N0 > 0.0)) {
     Landau<double> r;
     r.ok = false;
+    r.conv = false;
     return r;
   }
   const double is = rsqrt(NN);
-  return landau_from<double, 40>(m, m.N0 * is, m.Nx * is, m.Ny * is, m.Nz * is, 1e-12);
+  Landau<double> r = landau_from<double, 40>(m, m.N0 * is, m.Nx * is, m.Ny * is, m.Nz * is, 1e-12);
+  r.ok = r.ok && r.conv;  // no frame to 1e-12 in 40 double updates: reported, not used
+  return r;
 }
 
 // Landau matching in the step's arithmetic A.  Reduced-precision paths switch to double for cells
 // whose Eckart Lorentz factor exceeds gamma_thr (or always, if asked): the solve loses about
 // gamma^2 digits to cancellation in U.U = 1.
+// A double solve that stops at MAXIT without meeting its tolerance is accepted only if the last
+// update was below 1e-10 U0 (round-off can keep the last digits moving); a float solve that does
+// not converge in 8 updates is redone in double.
 template <class A>
 __device__ __forceinline__ Landau<A> landau_step(const Mom<A>& m, const StepParams& p) {
   if constexpr (std::is_same<A, double>::value) {
-    return landau<double, 40>(m);
+    Landau<double> r = landau<double, 40>(m);
+    if (r.ok && !r.conv) {
+      const Landau<double> again = landau_from<double, 1>(m, r.U0, r.Ux, r.Uy, r.Uz, 1e-10);
+      r.ok = again.ok && again.conv;
+    }
+    return r;
   } else {
     const float NN = m.N0 * m.N0 - m.Nx * m.Nx - m.Ny * m.Ny - m.Nz * m.Nz;
-    if (p.landau_fp64 || m.N0 * m.N0 > p.gamma_thr2 * NN) {
-      const Landau<double> d = landau_fp64_out_of_line(convert<A, double>(m));
-      return Landau<A>{(A)d.U0, (A)d.Ux, (A)d.Uy, (A)d.Uz, (A)d.eps, (A)d.n, d.ok};
+    Landau<float> r;
+    const bool dbl = p.landau_fp64 || m.N0 * m.N0 > p.gamma_thr2 * NN;
+    if (!dbl) {
+      r = landau<float, 8>(m);
+      if (r.conv || !r.ok) return r;
     }
-    return landau<float, 8>(m);
+    const Landau<double> d = landau_fp64_out_of_line(convert<A, double>(m));
+    return Landau<A>{(A)d.U0, (A)d.Ux, (A)d.Uy, (A)d.Uz, (A)d.eps, (A)d.n, d.ok, d.conv};
   }
 }
 
@@ -1004,18 +1024,32 @@ __global__ void __launch_bounds__(kMomThreads) k_fields(const typename S::T* __r
   const int gid = blockIdx.x * kMomThreads + threadIdx.x;
   const bool valid = gid < p.cells;
   const Cell cl = make_cell(valid ? gid : p.cells - 1, p);
-  auto get = [&](auto I) -> double {
+  auto index = [&](auto I) -> long long {
     constexpr int i = decltype(I)::value;
-    const long long idx = PULL ? pull_index<L, i, GENERAL, true>(cl, p) : (long long)i * p.cells + cl.c;
-    return S::template to_f64<L, i>(src[idx], p);
+    return PULL ? pull_index<L, i, GENERAL, true>(cl, p) : (long long)i * p.cells + cl.c;
   };
-  const Mom<double> m = moments<L, double>(get);
+  Mom<double> m;
   Landau<double> lw;
   if constexpr (std::is_same<typename S::A, double>::value) {
+    m = moments<L, double>([&](auto I) -> double { return src[index(I)]; });
     lw = landau<double, 200>(m);
   } else {
-    // float populations: start from the float solution, stop at 1e-12 U0 (float carries no more)
-    const Landau<float> lf = landau<float, 8>(convert<double, float>(m));
+    // float populations: the per-cell moments in float, as the step takes them (paired sums per
+    // direction; deviations for half storage); Landau matching from the float solution refined in
+    // double to 1e-12 U0 (float moments carry no more); the cross-cell sums below in double
+    constexpr bool DEV = std::is_same<S, StoreF16Dev>::value;
+    auto getf = [&](auto I) -> float {
+      constexpr int i = decltype(I)::value;
+      if constexpr (DEV) return S::template load_dev<L, i>(src + index(I), p);
+      else return (float)src[index(I)];
+    };
+    auto get2 = [&](auto I) -> float2 {
+      constexpr int i = decltype(I)::value;
+      return make_float2(getf(ic<i>{}), getf(ic<i + 1>{}));
+    };
+    const Mom<float> mf = moments_f2<L, DEV>(get2, p.half_nref);
+    m = convert<float, double>(mf);
+    const Landau<float> lf = landau<float, 8>(mf);
     if (lf.ok) lw = landau_from<double, 200>(m, (double)lf.U0, (double)lf.Ux, (double)lf.Uy, (double)lf.Uz, 1e-12);
     else lw = landau<double, 200>(m);
   }
@@ -1027,7 +1061,13 @@ __global__ void __launch_bounds__(kMomThreads) k_fields(const typename S::T* __r
     fields[3 * (long long)p.cells + cl.c] = lw.ok ? lw.Ux : nan;
     fields[4 * (long long)p.cells + cl.c] = lw.ok ? lw.Uy : nan;
     fields[5 * (long long)p.cells + cl.c] = lw.ok ? lw.Uz : nan;
-    if (!lw.ok) atomicAdd(&status[kStatusNonconv], 1);
+    // non-finite populations show as non-finite moments; any other cell without a frame is a
+    // Landau failure
+    const bool finite = isfinite(m.N0) && isfinite(m.Nx) && isfinite(m.Ny) && isfinite(m.Nz) && isfinite(m.T00) &&
+                        isfinite(m.T0x) && isfinite(m.T0y) && isfinite(m.T0z) && isfinite(m.Txx) &&
+                        isfinite(m.Tyy) && isfinite(m.Tzz) && isfinite(m.Txy) && isfinite(m.Txz) && isfinite(m.Tyz);
+    if (!finite) atomicAdd(&status[kStatusNan], 1);
+    else if (!lw.ok) atomicAdd(&status[kStatusNonconv], 1);
   }
   double d[5] = {valid ? m.N0 : 0.0, valid ? m.T00 : 0.0, valid ? m.T0x : 0.0, valid ? m.T0y : 0.0,
                  valid ? m.T0z : 0.0};
@@ -1050,8 +1090,8 @@ __global__ void __launch_bounds__(kMomThreads) k_fields(const typename S::T* __r
 }
 
 // ---------------------------------------------------------------------------------------------
-// initial state f_i = f_i^eq(n, T, u) (double arithmetic, per-level form), and population format
-// conversion
+// initial state f_i = f_i^eq(n, T, u) (per-level form: coefficients in double, Horner steps in the
+// storage's arithmetic), and population format conversion
 // ---------------------------------------------------------------------------------------------
 template <class L, class S>
 __global__ void __launch_bounds__(128) k_init(const double* __restrict__ n, const double* __restrict__ Tf,
@@ -1069,22 +1109,34 @@ __global__ void __launch_bounds__(128) k_init(const double* __restrict__ n, cons
   }
   const double g = rsqrt(1.0 - u2);
   const double Ux = g * ux, Uy = g * uy, Uz = g * uz;
-  // the equilibrium per energy level (see level_coef), in double
-  const LevCoef<L, double> e = level_coef<L, double>(eq_coef<L::ORDER, double>(nn, T, g));
+  // the equilibrium per energy level (see level_coef): coefficients in double; the per-population
+  // Horner steps in the storage's arithmetic (float storage: float, whose result is rounded to float
+  // anyway)
+  using A = typename S::A;
+  const LevCoef<L, double> ed = level_coef<L, double>(eq_coef<L::ORDER, double>(nn, T, g));
+  LevCoef<L, A> e;
+  static_for<L::NLEV>([&](auto K) {
+    constexpr int l = decltype(K)::value;
+    e.a[l] = (A)ed.a[l];
+    e.b[l] = (A)ed.b[l];
+    e.c[l] = (A)ed.c[l];
+    e.d[l] = (A)ed.d[l];
+  });
+  const A Uxa = (A)Ux, Uya = (A)Uy, Uza = (A)Uz;
   static_for<L::NDP>([&](auto K) {
     constexpr int k = decltype(K)::value;
     constexpr int first = L::DP_FIRST[k];
     constexpr int np = L::DP_NPAIR[k];
     constexpr int vx = L::VX[first], vy = L::VY[first], vz = L::VZ[first];
-    const double t = (vx * Ux + vy * Uy + vz * Uz) * L::INV_R;
+    const A t = (A(vx) * Uxa + A(vy) * Uya + A(vz) * Uza) * A(L::INV_R);
     static_for<np>([&](auto J) {
       constexpr int ip = first + 2 * decltype(J)::value;
       constexpr int l = L::LEV[ip];
       constexpr double w = L::W[ip];
-      const double Ep = fma(t, fma(t, fma(t, e.d[l], e.c[l]), e.b[l]), e.a[l]);
-      const double Em = fma(-t, fma(-t, fma(-t, e.d[l], e.c[l]), e.b[l]), e.a[l]);
-      S::template store<L, ip>(dst + (long long)ip * cells + c, (typename S::A)(w * Ep), p);
-      S::template store<L, ip + 1>(dst + (long long)(ip + 1) * cells + c, (typename S::A)(w * Em), p);
+      const A Ep = fma(t, fma(t, fma(t, e.d[l], e.c[l]), e.b[l]), e.a[l]);
+      const A Em = fma(-t, fma(-t, fma(-t, e.d[l], e.c[l]), e.b[l]), e.a[l]);
+      S::template store<L, ip>(dst + (long long)ip * cells + c, A(w) * Ep, p);
+      S::template store<L, ip + 1>(dst + (long long)(ip + 1) * cells + c, A(w) * Em, p);
     });
   });
 }

@@ -2,13 +2,14 @@
 // without allocating any memory.
 //
 // rlb_moments sums N^0 and T^{0 nu} through per-block partials that live in memory the context
-// allocated with cudaMalloc.  Some callers cannot allocate device memory at all: code running
-// inside a stream capture that must not add allocation nodes, plug-ins whose host application
-// owns every allocation, or processes that have reserved the whole device for their own pools.
-// This entry point keeps its scratch in a fixed array in the library's own device data segment,
-// which exists on every device that loads the library, from load until the process exits.
+// allocated with cudaMalloc.  Some callers cannot call the device allocator at all: plug-ins whose
+// host application owns every device allocation, processes that have reserved the whole device for
+// their own pools, or code under a hard memory budget.  This entry point keeps its scratch in a
+// fixed array in the library's own device data segment, which exists on every device that loads
+// the library, from load until the process exits.
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <string>
 
 #include "rlb.h"
@@ -25,7 +26,8 @@ constexpr int kNoallocMaxBlocks = RLB_NOALLOC_MAX_CELLS / kMomThreads;
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocMaxBlocks * 5 + 5];
 
 // Per-block sums of N^0, T^00, T^0x, T^0y, T^0z of the stored populations of each cell; the same
-// block size, warp shuffles and shared-memory tree as the fields kernel, written to partial[].
+// per-cell arithmetic, block size, warp shuffles and shared-memory tree as the fields kernel,
+// written to partial[].
 template <class L, class S>
 __global__ void __launch_bounds__(kMomThreads) k_densities_noalloc(const typename S::T* __restrict__ src,
                                                                    const __grid_constant__ StepParams p,
@@ -33,11 +35,24 @@ __global__ void __launch_bounds__(kMomThreads) k_densities_noalloc(const typenam
   const int gid = blockIdx.x * kMomThreads + threadIdx.x;
   const bool valid = gid < p.cells;
   const int c = valid ? gid : p.cells - 1;
-  auto get = [&](auto I) -> double {
-    constexpr int i = decltype(I)::value;
-    return S::template to_f64<L, i>(src[(long long)i * p.cells + c], p);
-  };
-  const Mom<double> m = moments<L, double>(get);
+  // per-cell moments in the arithmetic rlb_moments uses for this storage (double for double
+  // populations; paired float sums for float and half-deviation ones), summed across cells in double
+  Mom<double> m;
+  if constexpr (std::is_same<typename S::A, double>::value) {
+    m = moments<L, double>([&](auto I) -> double { return src[(long long)decltype(I)::value * p.cells + c]; });
+  } else {
+    constexpr bool DEV = std::is_same<S, StoreF16Dev>::value;
+    auto getf = [&](auto I) -> float {
+      constexpr int i = decltype(I)::value;
+      if constexpr (DEV) return S::template load_dev<L, i>(src + (long long)i * p.cells + c, p);
+      else return (float)src[(long long)i * p.cells + c];
+    };
+    auto get2 = [&](auto I) -> float2 {
+      constexpr int i = decltype(I)::value;
+      return make_float2(getf(ic<i>{}), getf(ic<i + 1>{}));
+    };
+    m = convert<float, double>(moments_f2<L, DEV>(get2, p.half_nref));
+  }
   double d[5] = {valid ? m.N0 : 0.0, valid ? m.T00 : 0.0, valid ? m.T0x : 0.0, valid ? m.T0y : 0.0,
                  valid ? m.T0z : 0.0};
 #pragma unroll
@@ -83,15 +98,19 @@ __global__ void __launch_bounds__(kReduceThreads) k_totals_noalloc(const double*
 }
 
 // Device address of the scratch array, looked up once per device with that device current.
-// In host code g_noalloc_scratch names a host-side stand-in, never the device array itself.
+// In host code g_noalloc_scratch names a host-side stand-in, never the device array itself.  The
+// per-device cache is guarded by a mutex: calls from several host threads see either no entry
+// (and one of them looks it up) or the finished one.
 constexpr int kMaxDevices = 64;
 double* g_scratch_ptr[kMaxDevices] = {nullptr};
+std::mutex g_scratch_mutex;
 
 cudaError_t scratch_for_current_device(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
   if (!g_scratch_ptr[dev]) {
     void* ptr = nullptr;
     e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);

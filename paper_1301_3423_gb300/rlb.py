@@ -165,6 +165,15 @@ def totals_noalloc(f, order, storage, shape, n_ref=1.0, stream=None):
     st_code = STORAGE[storage] if isinstance(storage, str) else int(storage)
     if not _is_cuda_tensor(f) or not f.is_contiguous():
         raise ValueError("f must be a contiguous CUDA tensor")
+    import torch
+    want = {0: torch.float64, 1: torch.float32, 2: torch.float16}.get(st_code)
+    q = {3: 128, 2: 66}.get(int(order))
+    if want is None or q is None:
+        raise ValueError("order must be 2 or 3 and storage one of %s" % sorted(STORAGE))
+    # the library reads q * cells elements of the storage type: check the buffer holds exactly that
+    if f.dtype != want or f.numel() != q * nx * ny * nz:
+        raise ValueError("f must hold %d x %d elements of %s, got %d of %s" % (q, nx * ny * nz, want, f.numel(),
+                                                                              f.dtype))
     tot = (ctypes.c_double * 5)()
     sp = None if stream is None else ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
     st = lib.rlb_totals_noalloc(order, st_code, nx, ny, nz, n_ref, ctypes.c_void_p(f.data_ptr()), tot, sp)

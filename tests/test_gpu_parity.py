@@ -72,6 +72,23 @@ def test_init_matches_oracle(order):
 
 
 @pytest.mark.parametrize("order", [3, 2])
+def test_f32_init_matches_oracle_to_float_rounding(order):
+    """Float storage: the equilibrium's coefficients in double, the per-population Horner steps in
+    float; every stored population within a few float units of the oracle's (1e-6 of the scale)."""
+    lat = oracle.read_lattice(order)
+    shape = (11, 13, 17)
+    n, T, u = gen.smooth_random_fields(shape, seed=21, vmax=0.6, sigma_lnT=0.2)
+    o = oracle.OracleRLB(lat, shape[2], shape[1], shape[0])
+    o.init(n, T, u)
+    with RLB(shape, order=order, storage="f32") as g:
+        g.init(n, T, u)
+        f = g.populations()
+    err = pop_err(lat, f, o.f, n.max())
+    print("f32 init order %d: max population error %.2e" % (order, err))
+    assert err < 1e-6
+
+
+@pytest.mark.parametrize("order", [3, 2])
 @pytest.mark.parametrize("bc", ["periodic", "copyout_z", "copyout_xy", "walls_xz", "box"])
 def test_f64_steps_match_oracle(order, bc):
     """17 x 13 x 11 cells: 19 blocks of 128 threads with a ragged last block; interior warps take
@@ -327,3 +344,22 @@ def test_full_size_sampled_cells(storage, tol, variant, bc):
     err = float(np.max(np.abs(got - ref) / scale))
     print("full-size %s variant %d %s sampled error %.2e" % (storage, variant, bc, err))
     assert err < tol
+
+
+def test_non_finite_populations_are_reported_as_enan():
+    """A NaN population makes the cell's moments non-finite: rlb_moments reports RLB_ENAN (not a
+    Landau failure), and the context stays usable."""
+    lat = oracle.read_lattice(3)
+    shape = (4, 5, 6)
+    f0 = near_equilibrium(lat, shape, seed=2)
+    bad = f0.copy()
+    bad[7, 1, 2, 3] = np.nan
+    with RLB(shape, tau_prime=1.0) as g:
+        g.set_populations(bad)
+        with pytest.raises(RLBError) as e:
+            g.moments()
+        assert e.value.status == rlbmod.RLB_ENAN
+        assert "1 cells with non-finite" in str(e.value)
+        g.set_populations(f0)
+        g.step(2)
+        g.moments()  # clean again

@@ -13,8 +13,10 @@ from paper_1301_3423_gb300 import serve  # noqa: E402
 
 
 def solo(req, landau_fp64):
+    """The request run alone with the kernels the server's batches use (the register step kernel,
+    variant 0, which the batched kernel reproduces bitwise)."""
     with RLB(req.shape, order=3, bc=req.bc, eta_over_s=req.eta_over_s, storage=req.storage,
-             landau_fp64=landau_fp64) as c:
+             landau_fp64=landau_fp64, step_variant=0) as c:
         c.init(*serve.initial_fields(req))
         c.step(req.steps)
         return c.moments()
