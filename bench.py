@@ -3,7 +3,8 @@
 Workload (one "step" = one time step of the whole lattice through the fused pull-collide kernel):
 the 256^3 periodic random-field case of the third-order model (Q = 128) with float storage:
 velocity from Fourier modes |k| <= 4 rescaled to max |v| = 0.6, log-normal temperature
-(sigma 0.2, mean 1), n = T^3, eta/s = 0.1 with the local-temperature relaxation time.
+(sigma 0.2, mean 1), uniform density n = 1 (the n = T^3 variant of this case loses its Landau
+frames in 3D; see the design notes), eta/s = 0.1 with the local-temperature relaxation time.
 
 Prints one JSON line:
   value      MLUPS (million lattice-cell updates per second) with the state resident in HBM;
@@ -11,6 +12,11 @@ Prints one JSON line:
              (rlb_init from host fields, K steps, rlb_moments back to host);
   roofline   the step kernel's algorithmic bytes (Q x 2 x 4 bytes per cell update) per launch over
              its CUDA-event duration, against the measured HBM copy bandwidth;
+  batched    64 uneven instances at their full step counts in persistent batched launches,
+             against the same instances one at a time and against double storage (solves/s and
+             the float-vs-double field error per instance of a subset);
+  serving    a Poisson request stream plus three 384^3 requests under a 150 GB budget (p50/p99
+             time to solution, peak device bytes, requests that waited for memory);
   cpu_baseline  the FP64 oracle on the host cores, on a bounded sample of the same workload;
   fp64_plain the same lattice with double storage and arithmetic (MLUPS).
 
@@ -142,6 +148,15 @@ def recorded_traffic(n_side, variant, density, path=None):
     return rec.get("dram_bytes_per_step")
 
 
+def step_kernel_name(variant):
+    """The kernels one time step of float storage launches with this variant."""
+    from paper_1301_3423_gb300.rlb import VARIANT_NAMES
+    name = VARIANT_NAMES[variant] if 0 <= variant < len(VARIANT_NAMES) else str(variant)
+    if variant >= 4:
+        return "k_step_pipe<Quad3, StoreF32> (%s; one launch per step)" % name
+    return "k_step_interior + k_step_shell_rows <Quad3, StoreF32, variant %d> (%s)" % (variant, name)
+
+
 def dist_env():
     """(world, rank, local rank) from the torchrun environment (1, 0, 0 without it)."""
     return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
@@ -203,8 +218,27 @@ def cpu_baseline(n, T, u, budget_s=12.0, planes=2):
     dt = time.perf_counter() - t0
     cells = nx * ny * nz
     return {"value": cells * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "host_cores": os.cpu_count(), "cpu_model": cpu_model(),
             "sample": "%d steps of the first %d z-planes of the %dx%dx%d workload as a periodic %dx%dx%d slab "
                       "(%d cells; serial FP64 C oracle, %.1f s)" % (steps, planes, nx, ny, nx, nx, ny, nz, cells, dt)}
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or None."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
 
 
 def field_errors(ref, got):
@@ -254,15 +288,19 @@ def make_instance(spec, storage, variant=-1, stream=None, landau_fp64=False):
 
 
 def run_batched(args, stream):
-    """64 uneven instances stepped together (persistent tile-queue kernel, CUDA-graph step loops),
-    against the same instances stepped one at a time in float and in double."""
+    """64 uneven instances stepped together (persistent tile-queue kernels, CUDA-graph step loops),
+    against the same instances stepped one at a time in float and in double.  Double storage is
+    timed on a subset of 8 instances spread over the mix (it runs at ~0.2 G updates/s), which also
+    gives the float-vs-double field error of each of those instances."""
     import torch
 
     from paper_1301_3423_gb300 import Batch
     specs = batched_instances(args.batch_scale)
     updates = float(sum(np.prod(sp[1]) * sp[4] for sp in specs))
+    order = sorted(range(len(specs)), key=lambda k: np.prod(specs[k][1]) * specs[k][4])
+    sub = [order[int(round(j * (len(order) // 2 - 1) / 7))] for j in range(8)]  # smaller half of the mix
 
-    def batched_run(landau_fp64, variant=None):
+    def batched_run(landau_fp64, variant=None, keep=()):
         ctxs = [make_instance(sp, "f32", stream=stream, landau_fp64=landau_fp64) for sp in specs]
         b = Batch(ORDER, "f32", stream=stream)
         for c, sp in zip(ctxs, specs):
@@ -278,59 +316,86 @@ def run_batched(args, stream):
             active = b.run(25, graph=True)
         torch.cuda.synchronize()
         t = time.perf_counter() - t0
-        for c in ctxs:
+        kept = {}
+        for k, c in enumerate(ctxs):
+            if k in keep:
+                kept[k] = c.moments()
             c.sync()
             c.close()
         launches = b.kernel_launches
         b.close()
-        return t, variant, launches
+        return t, variant, launches, kept
 
-    t_batch, variant, launches = batched_run(False)
-    t_batch_d, _, _ = batched_run(True, variant)
+    t_batch, variant, launches, fields32 = batched_run(False, keep=set(sub))
+    t_batch_d, _, _, _ = batched_run(True, variant)
     t_seq = 0.0  # only the stepping counts, as for the batch
     for sp in specs:
-        c = make_instance(sp, "f32", variant=variant, stream=stream)
+        c = make_instance(sp, "f32", stream=stream)
         c.sync()
         t1 = time.perf_counter()
         c.step(sp[4])
         c.sync()
         t_seq += time.perf_counter() - t1
         c.close()
-    sub = specs[:8]  # double storage is FP64-ALU bound: timed on the first 8 instances
-    u64 = float(sum(np.prod(sp[1]) * sp[4] for sp in sub))
+    u64 = float(sum(np.prod(specs[k][1]) * specs[k][4] for k in sub))
     t64 = 0.0
-    for sp in sub:
-        c = make_instance(sp, "f64", stream=stream)
+    errs = []
+    for k in sub:
+        c = make_instance(specs[k], "f64", stream=stream)
         c.sync()
         t1 = time.perf_counter()
-        c.step(sp[4])
+        c.step(specs[k][4])
         c.sync()
         t64 += time.perf_counter() - t1
+        e = field_errors(c.moments(), fields32[k])
+        errs.append(dict(kind=specs[k][0], shape=list(specs[k][1]), steps=specs[k][4], eta_over_s=specs[k][3], **e))
         c.close()
+    worst = max(max(e["n_rel"], e["eps_rel"], e["u_rel"]) for e in errs)
     return {"instances": len(specs), "cell_updates": updates, "step_scale": args.batch_scale,
             "value": updates / t_batch / 1e6, "unit": "MLUPS", "seconds": t_batch, "solves_per_s": len(specs) / t_batch,
+            "hbm_frac": updates * Q * 2 * 4 / t_batch / 1e9 / measured_peaks()[0]["hbm_gbs"],
             "variant": variant, "kernel_launches": launches, "graph_steps": 25,
             "landau": "float, double above gamma_thr = 2",
             "fp64_landau_every_cell": {"value": updates / t_batch_d / 1e6, "seconds": t_batch_d,
                                        "solves_per_s": len(specs) / t_batch_d},
             "sequential_f32": {"value": updates / t_seq / 1e6, "seconds": t_seq, "solves_per_s": len(specs) / t_seq},
             "fp64_plain": {"value": u64 / t64 / 1e6, "instances": len(sub), "seconds": t64,
-                           "solves_per_s_est": len(specs) / (t64 * updates / u64)}}
+                           "solves_per_s_est": len(specs) / (t64 * updates / u64),
+                           "estimate": "the subset's double-storage rate applied to the whole mix"},
+            "f32_batched_vs_f64_plain": {"max_rel_err": worst, "bar": 1e-5, "per_instance": errs}}
 
 
 def run_serving(args, stream):
-    """Poisson request stream (mean 20 / s) through the continuous-batching server."""
+    """Poisson request stream (mean 20 / s, 40 requests, sides up to 384 drawn with probability
+    proportional to 1/L^3, full step counts) plus three 384^3 float shear-wave requests (2000 steps)
+    early in the stream, through the continuous-batching server under a 150 GB budget: two 384^3
+    lattices fit (58 GB each), the third waits for memory."""
     from paper_1301_3423_gb300 import serve
-    reqs = serve.poisson_requests(60, rate=20.0, seed=5, step_scale=args.batch_scale, f16_fraction=0.3)
+    reqs = serve.poisson_requests(40, rate=20.0, seed=5, step_scale=args.batch_scale, f16_fraction=0.3)
+    for j, t in enumerate((0.0, 0.02, 0.04)):
+        reqs.append(serve.Request(1000 + j, "shear", (384, 384, 384), 0.1, max(1, int(round(2000 * args.batch_scale))),
+                                  "f32", 77 + j, t))
     srv = serve.Server(hbm_budget=150e9, chunk=25, stream=stream)
     try:
-        st = srv.run(reqs, realtime=True, max_wall=600)
+        st = srv.run(reqs, realtime=True, max_wall=900)
     finally:
         srv.close()
+    big = [r.tts for r in srv.results if r.rid >= 1000 and r.status == "ok"]
     st.update({"rate_per_s": 20.0, "step_scale": args.batch_scale,
                "largest_side": max(max(r.shape) if r.kind != "tube" else 0 for r in reqs),
-               "f16dev_requests": sum(r.storage == "f16dev" for r in reqs)})
+               "f16dev_requests": sum(r.storage == "f16dev" for r in reqs),
+               "tts_384_s": big, "solo_cells": srv.solo_cells})
     return st
+
+
+def workload_config(args, world):
+    """The benchmark workload's config (the same for this arm and the reference arm)."""
+    N = args.n
+    return {"workload": WORKLOAD % N, "lattice": [N, N, N], "order": ORDER, "q": Q, "storage": "f32",
+            "eta_over_s": ETA_S, "max_v": 0.6, "sigma_lnT": args.sigma, "density": args.density,
+            "boundary": "periodic", "parallelism": "replicas" if world > 1 else "single",
+            "l2": "inputs larger than L2: two population buffers of %.1f GB" % (N ** 3 * Q * 4 / 1e9),
+            "baseline_metric": BASELINE_METRIC}
 
 
 def run_reference(args, world, rank):
@@ -342,9 +407,7 @@ def run_reference(args, world, rank):
     cb = cpu_baseline(n, T, u, budget_s=budget)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": (WORKLOAD % N).replace("FP32 storage", "FP64 CPU oracle"), "sample": cb["sample"],
-                       "sigma_lnT": args.sigma, "density": args.density},
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args, world),
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -364,7 +427,7 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--batch-scale", type=float, default=0.1,
+    ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="fraction of the batched / served step counts (500 / 2000 / 1000) to run")
     ap.add_argument("--density", default=DENSITY, choices=["uniform", "cube"],
                     help="initial density: uniform n = 1, or n = T^3")
@@ -496,14 +559,11 @@ def main():
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD % N, "lattice": [N, N, N], "order": ORDER, "q": Q, "storage": "f32",
-                   "eta_over_s": ETA_S, "max_v": 0.6, "sigma_lnT": args.sigma, "density": args.density, "boundary": "periodic", "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2: two population buffers of %.1f GB" % (cells * Q * 4 / 1e9),
-                   "baseline_metric": BASELINE_METRIC},
+        "config": workload_config(args, world),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                      "peak_source": peak_src, "algorithmic_bytes_per_step": algo_bytes,
-                     "kernel": "k_step_interior + k_step_shell_rows <Quad3, StoreF32, variant %d>" % variant,
+                     "kernel": step_kernel_name(variant),
                      "step_ms": per_step_s * 1e3, "launches_per_step": launches / args.steps},
         "cpu_baseline": cb,
         "e2e": e2e,

@@ -1090,6 +1090,59 @@ __global__ void __launch_bounds__(kMomThreads) k_fields(const typename S::T* __r
 }
 
 // ---------------------------------------------------------------------------------------------
+// float-float arithmetic: a value as the unevaluated sum hi + lo of two floats (|lo| <= ulp(hi)/2),
+// built from the error-free transformations of Dekker and Knuth (two-sum; two-product by FMA).
+// About 44 bits of significand, at float-pipe speed.
+// ---------------------------------------------------------------------------------------------
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_from(double x) {
+  const float hi = (float)x;
+  return FF{hi, (float)(x - (double)hi)};
+}
+
+__device__ __forceinline__ FF ff_neg(FF a) { return FF{-a.hi, -a.lo}; }
+
+// hi + lo of a + b exactly (Knuth's two-sum)
+__device__ __forceinline__ FF two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return FF{s, (a - (s - bb)) + (b - bb)};
+}
+
+__device__ __forceinline__ FF fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return FF{s, b - (s - a)};
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const FF s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  const float p = a.hi * b.hi;
+  const float e = fmaf(a.hi, b.hi, -p);  // exact error of the product
+  return fast_two_sum(p, e + fmaf(a.hi, b.lo, a.lo * b.hi));
+}
+
+// a times a small integer k (|k| <= 6): exact in float-float
+__device__ __forceinline__ FF ff_scale(FF a, float k) {
+  const float p = a.hi * k;
+  return fast_two_sum(p, fmaf(a.hi, k, -p) + a.lo * k);
+}
+
+// a + t (b + t (c + t d)) in float-float, rounded to float
+__device__ __forceinline__ float ff_horner3(FF t, FF a, FF b, FF c, FF d) {
+  FF r = ff_add(ff_mul(d, t), c);
+  r = ff_add(ff_mul(r, t), b);
+  r = ff_add(ff_mul(r, t), a);
+  return r.hi + r.lo;
+}
+
+// ---------------------------------------------------------------------------------------------
 // initial state f_i = f_i^eq(n, T, u) (per-level form: coefficients in double, Horner steps in the
 // storage's arithmetic), and population format conversion
 // ---------------------------------------------------------------------------------------------
@@ -1109,36 +1162,67 @@ __global__ void __launch_bounds__(128) k_init(const double* __restrict__ n, cons
   }
   const double g = rsqrt(1.0 - u2);
   const double Ux = g * ux, Uy = g * uy, Uz = g * uz;
-  // the equilibrium per energy level (see level_coef): coefficients in double; the per-population
-  // Horner steps in the storage's arithmetic (float storage: float, whose result is rounded to float
-  // anyway)
-  using A = typename S::A;
+  // the equilibrium per energy level (see level_coef), coefficients in double
   const LevCoef<L, double> ed = level_coef<L, double>(eq_coef<L::ORDER, double>(nn, T, g));
-  LevCoef<L, A> e;
-  static_for<L::NLEV>([&](auto K) {
-    constexpr int l = decltype(K)::value;
-    e.a[l] = (A)ed.a[l];
-    e.b[l] = (A)ed.b[l];
-    e.c[l] = (A)ed.c[l];
-    e.d[l] = (A)ed.d[l];
-  });
-  const A Uxa = (A)Ux, Uya = (A)Uy, Uza = (A)Uz;
-  static_for<L::NDP>([&](auto K) {
-    constexpr int k = decltype(K)::value;
-    constexpr int first = L::DP_FIRST[k];
-    constexpr int np = L::DP_NPAIR[k];
-    constexpr int vx = L::VX[first], vy = L::VY[first], vz = L::VZ[first];
-    const A t = (A(vx) * Uxa + A(vy) * Uya + A(vz) * Uza) * A(L::INV_R);
-    static_for<np>([&](auto J) {
-      constexpr int ip = first + 2 * decltype(J)::value;
-      constexpr int l = L::LEV[ip];
-      constexpr double w = L::W[ip];
-      const A Ep = fma(t, fma(t, fma(t, e.d[l], e.c[l]), e.b[l]), e.a[l]);
-      const A Em = fma(-t, fma(-t, fma(-t, e.d[l], e.c[l]), e.b[l]), e.a[l]);
-      S::template store<L, ip>(dst + (long long)ip * cells + c, A(w) * Ep, p);
-      S::template store<L, ip + 1>(dst + (long long)(ip + 1) * cells + c, A(w) * Em, p);
+  if constexpr (std::is_same<typename S::A, double>::value) {
+    static_for<L::NDP>([&](auto K) {
+      constexpr int k = decltype(K)::value;
+      constexpr int first = L::DP_FIRST[k];
+      constexpr int np = L::DP_NPAIR[k];
+      constexpr int vx = L::VX[first], vy = L::VY[first], vz = L::VZ[first];
+      const double t = (vx * Ux + vy * Uy + vz * Uz) * L::INV_R;
+      static_for<np>([&](auto J) {
+        constexpr int ip = first + 2 * decltype(J)::value;
+        constexpr int l = L::LEV[ip];
+        constexpr double w = L::W[ip];
+        const double Ep = fma(t, fma(t, fma(t, ed.d[l], ed.c[l]), ed.b[l]), ed.a[l]);
+        const double Em = fma(-t, fma(-t, fma(-t, ed.d[l], ed.c[l]), ed.b[l]), ed.a[l]);
+        S::template store<L, ip>(dst + (long long)ip * cells + c, w * Ep, p);
+        S::template store<L, ip + 1>(dst + (long long)(ip + 1) * cells + c, w * Em, p);
+      });
     });
-  });
+  } else {
+    // Float storage rounds every population to float.  The cubic in t cancels strongly at the high
+    // energy levels (terms up to ~200 times the value at p0 = 10.95, |u| = 0.6), so those levels
+    // (p0 > 4) are evaluated in float-float arithmetic (a value as an unevaluated sum hi + lo of
+    // two floats; error-free sums and products by FMA), the others in float: every population ends
+    // within float rounding of the double evaluation, with no double arithmetic per population.
+    LevCoef<L, FF> e;
+    static_for<L::NLEV>([&](auto K) {
+      constexpr int l = decltype(K)::value;
+      e.a[l] = ff_from(ed.a[l]);
+      e.b[l] = ff_from(ed.b[l]);
+      e.c[l] = ff_from(ed.c[l]);
+      e.d[l] = ff_from(ed.d[l]);
+    });
+    const FF Uxf = ff_from(Ux), Uyf = ff_from(Uy), Uzf = ff_from(Uz);
+    static_for<L::NDP>([&](auto K) {
+      constexpr int k = decltype(K)::value;
+      constexpr int first = L::DP_FIRST[k];
+      constexpr int np = L::DP_NPAIR[k];
+      constexpr int vx = L::VX[first], vy = L::VY[first], vz = L::VZ[first];
+      // t = v.U / R: exact small-integer multiples, float-float sum and scaling
+      const FF t = ff_mul(ff_add(ff_add(ff_scale(Uxf, (float)vx), ff_scale(Uyf, (float)vy)), ff_scale(Uzf, (float)vz)),
+                          ff_from(L::INV_R));
+      static_for<np>([&](auto J) {
+        constexpr int ip = first + 2 * decltype(J)::value;
+        constexpr int l = L::LEV[ip];
+        constexpr float w = (float)L::W[ip];
+        float Ep, Em;
+        if constexpr (L::P0[l] > 4.0) {
+          const FF tm = ff_neg(t);
+          Ep = ff_horner3(t, e.a[l], e.b[l], e.c[l], e.d[l]);
+          Em = ff_horner3(tm, e.a[l], e.b[l], e.c[l], e.d[l]);
+        } else {
+          const float tf = t.hi + t.lo;
+          Ep = fmaf(tf, fmaf(tf, fmaf(tf, e.d[l].hi, e.c[l].hi), e.b[l].hi), e.a[l].hi);
+          Em = fmaf(-tf, fmaf(-tf, fmaf(-tf, e.d[l].hi, e.c[l].hi), e.b[l].hi), e.a[l].hi);
+        }
+        S::template store<L, ip>(dst + (long long)ip * cells + c, w * Ep, p);
+        S::template store<L, ip + 1>(dst + (long long)(ip + 1) * cells + c, w * Em, p);
+      });
+    });
+  }
 }
 
 // double[q][cells] <-> storage, for populations [i0, i1) (in-range cells only)
