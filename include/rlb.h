@@ -174,12 +174,17 @@ rlb_status rlb_autotune(rlb_ctx* ctx, int reps, int* variant, double ms[RLB_MAX_
 
 /* ---------------------------------------------------------------------------------------------
  * Batched stepping.  A batch steps many contexts of the same order and storage together: each
- * time step of Eq. (rlb:disc) is two launches of persistent kernels that advance every member
- * with steps left, taking tiles from queues shared by all members (first the members' interior
- * rows in 32-cell segments, four per tile, then their boundary cells, 128 per tile), so lattices of
- * very different sizes fill the GPU together.  Members keep their own buffers, parameters, status
- * and step counters; a member's populations after a batched run are bitwise those of the same
- * steps taken alone with the same step-kernel variant.  Members must use the batch's stream.
+ * time step of Eq. (rlb:disc) is one launch of persistent kernels per kernel kind, advancing every
+ * member with steps left over tiles shared by all members, so lattices of very different sizes
+ * fill the GPU together.  With a register variant (0..3) every member goes through the register
+ * kernels (two launches: the members' interior rows in 32-cell segments, four per tile, then their
+ * boundary cells).  With a pipelined variant (4 and up) the members whose rows start on 16-byte
+ * boundaries go through one launch of the batched pipelined kernel over their row segments, and
+ * the others (e.g. 1 x 1 x N tubes) through the register kernels with the variant a context of
+ * that storage runs when it has no pipelined one (3 float, 2 half, 0 double).  Members keep their
+ * own buffers, parameters, status and step counters; a member's populations after a batched run
+ * are bitwise those of the same steps taken alone with the same step-kernel variant.  Members must
+ * use the batch's stream.
  * ------------------------------------------------------------------------------------------- */
 typedef struct rlb_batch rlb_batch;
 
@@ -211,8 +216,8 @@ rlb_status rlb_batch_run(rlb_batch* b, long nsteps, int use_graph, int* active);
  * fastest.  *variant and ms[RLB_MAX_VARIANTS] as for rlb_autotune. */
 rlb_status rlb_batch_autotune(rlb_batch* b, int reps, int* variant, double ms[RLB_MAX_VARIANTS]);
 
-/* Force the batched kernel's step variant (numbered as for rlb_autotune).
- * Errors: RLB_EINVAL for a variant the batch's storage does not have. */
+/* Force the batch's step variant (numbered as for rlb_autotune; see above for how members are
+ * split between kernels).  Errors: RLB_EINVAL for a variant the batch's storage does not have. */
 rlb_status rlb_batch_set_variant(rlb_batch* b, int variant);
 
 /* Kernel launches the batch has enqueued (-1 for NULL). */

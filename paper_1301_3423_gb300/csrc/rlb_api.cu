@@ -157,43 +157,20 @@ static bool needs_general_wrap(const rlb_params& p) {
          (p.bc[2] == RLB_BC_PERIODIC && p.nz < L::VMAX_Z);
 }
 
-// Shape of pipelined variant v (>= kNumRegVariants) on this context's lattice: the tiles, the
-// stages that fit the shared memory of one block, the launch.  False if the variant does not exist
-// or the lattice cannot use it (rows must start on 16-byte boundaries, at least one stage per
-// consumer group plus one in flight).
-static bool pipe_shape(const rlb_ctx* c, int v, PipeParams* pp, int* grid, int* threads, int* smem) {
-  if (v < kNumRegVariants || v >= kNumVariantsTotal) return false;
-  const PipeConfig& cf = kPipeConfigs[v - kNumRegVariants];
-  const int A = 16 / (int)c->elem;
-  if (c->sp.nx % A != 0 || c->sms <= 0) return false;
-  const long long stage = (long long)c->q * (cf.tx + A) * (long long)c->elem;
-  const long long budget = std::min<long long>(c->smem_optin, c->smem_per_sm / cf.ctas_per_sm - 1024);
-  // float storage splits each cell between a pair of consumer warps
-  const bool split = c->elem == 4;
-  const int wpt = cf.tx / 32 * (split ? 2 : 1);
-  const int groups = cf.cons_warps / wpt;
-  if (groups < 1 || cf.cons_warps % wpt != 0 || cf.producers < 1) return false;
-  const long long xchg = split ? (long long)cf.cons_warps / 2 * kPipeXchgBytesPerPair : 0;
-  // stages: the largest multiple of the group count that fits, at least two per group
-  const int fit = (int)std::min<long long>(kPipeMaxStages, (budget - kPipeHeaderBytes - xchg) / stage);
-  const int nstage = fit / groups * groups;
-  if (nstage < 2 * groups || cf.producers > c->q) return false;
-  PipeParams r{};
-  r.segs = (c->sp.nx + cf.tx - 1) / cf.tx;
-  const long long ntiles = (long long)r.segs * c->sp.ny * c->sp.nz;
+// Shape of pipelined variant v (>= kNumRegVariants) on this context's lattice: the block layout
+// (pipe_layout) and the tiles.  False if the variant does not exist or the lattice cannot use it
+// (rows must start on 16-byte boundaries).
+static bool pipe_shape(const rlb_ctx* c, int v, PipeParams* pp, int* grid, int* threads, int* smem, int* tx = nullptr) {
+  PipeLayout lay;
+  if (c->sms <= 0 || !pipe_layout(v, c->q, (int)c->elem, c->smem_per_sm, c->smem_optin, &lay)) return false;
+  if (c->sp.nx % (16 / (int)c->elem) != 0) return false;
+  const long long ntiles = (long long)((c->sp.nx + lay.tx - 1) / lay.tx) * c->sp.ny * c->sp.nz;
   if (ntiles > 0x7fffffffll) return false;
-  r.ntiles = (int)ntiles;
-  r.nstage = nstage;
-  r.groups = groups;
-  r.xperiodic = c->sp.bc[0] == kPeriodic ? 1 : 0;
-  r.producers = cf.producers;
-  if (cf.producers > kPipeMaxProducerWarps || cf.cons_warps > kPipeMaxConsumerWarps ||
-      cf.cons_warps + cf.producers > kPipeMaxWarps)
-    return false;
-  if (pp) *pp = r;
-  if (grid) *grid = (int)std::min<long long>((long long)c->sms * cf.ctas_per_sm, ntiles);
-  if (threads) *threads = (cf.cons_warps + cf.producers) * 32;
-  if (smem) *smem = (int)(kPipeHeaderBytes + nstage * stage + xchg);
+  if (pp) *pp = PipeParams{lay.producers, (int)ntiles, lay.nstage, lay.groups};
+  if (grid) *grid = (int)std::min<long long>((long long)c->sms * lay.ctas_per_sm, ntiles);
+  if (threads) *threads = lay.threads;
+  if (smem) *smem = lay.smem;
+  if (tx) *tx = lay.tx;
   return true;
 }
 
@@ -225,11 +202,11 @@ static rlb_status check_launch(rlb_ctx* c, cudaError_t e, const char* what);
 static rlb_status launch_step(rlb_ctx* c, int v) {
   if (v >= kNumRegVariants) {
     PipeParams pp;
-    int grid = 0, threads = 0, smem = 0;
-    if (!pipe_shape(c, v, &pp, &grid, &threads, &smem)) return fail(c, RLB_EINVAL, "step variant not available");
+    int grid = 0, threads = 0, smem = 0, tx = 0;
+    if (!pipe_shape(c, v, &pp, &grid, &threads, &smem, &tx)) return fail(c, RLB_EINVAL, "step variant not available");
     return check_launch(c,
-                        c->launch->pipe_step(c->buf[c->cur], c->buf[1 - c->cur], c->sp, pp, c->status,
-                                             kPipeConfigs[v - kNumRegVariants].tx, grid, threads, smem, c->stream),
+                        c->launch->pipe_step(c->buf[c->cur], c->buf[1 - c->cur], c->sp, pp, c->status, tx, grid,
+                                             threads, smem, c->stream),
                         "pipelined step kernel");
   }
   rlb_status st = check_launch(

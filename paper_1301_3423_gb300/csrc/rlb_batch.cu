@@ -25,7 +25,7 @@ struct Member {
 struct GraphCache {
   cudaGraphExec_t exec = nullptr;
   long nsteps = 0, version = -1;
-  int variant = -1, nmembers = 0, tiles = 0, row_tiles = -1, walls = -1;
+  int variant = -1, nmembers = 0, tiles = 0, row_tiles = -1, walls = -1, pipe_tiles = -1, pipe_walls = -1;
 };
 
 }  // namespace
@@ -41,10 +41,17 @@ struct rlb_batch {
   int* d_counters = nullptr;     // two tile counters (row queue, shell queue) per step of a run
   long counters_capacity = 0;
   const Launchers* launch = nullptr;
-  int variant = 0;
-  int walls = 0;                 // some member of the uploaded table has bounce-back walls
+  int variant = 0;               // step variant: 0..3 register kernels for every member; 4 and up the
+                                 // pipelined kernel for members whose rows start on 16-byte boundaries
+                                 // and the register fallback (reg_fallback) for the others
+  int walls = 0;                 // some register-kernel member of the uploaded table has bounce-back walls
   int row_tiles = 0, shell_tiles = 0;  // of the uploaded table: row tiles first, then shell tiles
-  int sms = 0;
+  int* d_pipe_tm = nullptr;      // member index of every pipelined tile of the uploaded table
+  int pipe_tm_capacity = 0;
+  int pipe_tiles = 0, pipe_walls = 0;
+  int* pipe_timeout = nullptr;   // status word that counts the pipelined kernel's expired waits
+  PipeLayout lay{};              // block layout of the current pipelined variant
+  int sms = 0, smem_per_sm = 0, smem_optin = 0;
   long version = 0;              // bumps when the member set changes
   long launches = 0;
   GraphCache graph;
@@ -80,9 +87,28 @@ extern "C" rlb_status rlb_batch_create(int order, int storage, void* stream, rlb
     delete b;
     return RLB_ECUDA;
   }
+  if (cudaDeviceGetAttribute(&b->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&b->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return RLB_ECUDA;
+  }
   b->variant = storage == RLB_F64 ? 0 : kDefaultStepVariant;
   *out = b;
   return RLB_OK;
+}
+
+static int elem_of(int storage) { return storage == RLB_F64 ? 8 : (storage == RLB_F32 ? 4 : 2); }
+
+// The register-kernel variant for members the pipelined kernel cannot take (rows not on 16-byte
+// boundaries): the one a context of that storage runs when no pipelined variant exists for it.
+static int reg_fallback(const rlb_batch* b) { return b->storage == RLB_F32 ? 3 : (b->storage == RLB_F16DEV ? 2 : 0); }
+
+static bool variant_exists(const rlb_batch* b, int v, PipeLayout* lay = nullptr) {
+  if (v < 0) return false;
+  if (v < kNumRegVariants) return v < b->launch->step_variants;
+  const int q = b->order == 3 ? 128 : 66;
+  return pipe_layout(v, q, elem_of(b->storage), b->smem_per_sm, b->smem_optin, lay);
 }
 
 extern "C" rlb_status rlb_batch_add(rlb_batch* b, rlb_ctx* ctx, long steps, int* slot) {
@@ -122,11 +148,17 @@ extern "C" long rlb_batch_steps_left(const rlb_batch* b, int slot) {
   return b->members[slot].steps_left;
 }
 
-// Member table of a run: the active members in slot order with their tile ranges.
-static rlb_status upload_table(rlb_batch* b, long nsteps, int* nmembers, int* total_tiles) {
+// Member table of a run with step variant `variant`: the active members in slot order with their
+// tile ranges (pipelined tiles for the members the pipelined kernel takes, register-kernel row and
+// shell tiles for the others).
+static rlb_status upload_table(rlb_batch* b, long nsteps, int variant, int* nmembers, int* total_tiles) {
   std::vector<BatchMember> t;
-  std::vector<int> row_tm, shell_tm;
+  std::vector<int> row_tm, shell_tm, pipe_tm;
   b->walls = 0;
+  b->pipe_walls = 0;
+  b->pipe_timeout = nullptr;
+  const bool pipe = variant >= kNumRegVariants && variant_exists(b, variant, &b->lay);
+  const int A = 16 / elem_of(b->storage);
   for (const Member& m : b->members) {
     if (!m.ctx || m.steps_left <= 0) continue;
     BatchMember d{};
@@ -136,6 +168,17 @@ static rlb_status upload_table(rlb_batch* b, long nsteps, int* nmembers, int* to
     d.status = m.ctx->status;
     d.parity0 = m.ctx->cur;
     d.steps_left = (int)std::min<long>(m.steps_left, nsteps);
+    if (pipe && d.p.nx % A == 0) {
+      // pipelined: ceil(nx / TX) tiles per row
+      d.pipe_tile_begin = (int)pipe_tm.size();
+      const long long nt = (long long)((d.p.nx + b->lay.tx - 1) / b->lay.tx) * d.p.ny * d.p.nz;
+      if ((long long)pipe_tm.size() + nt > 0x7fffffffll) return bfail(b, RLB_EINVAL, "too many tiles in one batch");
+      pipe_tm.resize(pipe_tm.size() + nt, (int)t.size());
+      if (d.p.has_wall) b->pipe_walls = 1;
+      if (!b->pipe_timeout) b->pipe_timeout = d.status + kStatusTimeout;
+      t.push_back(d);
+      continue;
+    }
     if (d.p.has_wall) b->walls = 1;
     // row tiles: 4 row-kernel warps; shell tiles: 4 shell-row warps (kStepThreads shell cells for
     // members that need the modulo wrap)
@@ -149,13 +192,29 @@ static rlb_status upload_table(rlb_batch* b, long nsteps, int* nmembers, int* to
   }
   b->row_tiles = (int)row_tm.size();
   b->shell_tiles = (int)shell_tm.size();
+  b->pipe_tiles = (int)pipe_tm.size();
   for (BatchMember& d : t) d.shell_tile_begin += b->row_tiles;
   std::vector<int> tm(row_tm);
   tm.insert(tm.end(), shell_tm.begin(), shell_tm.end());
   const int tiles = (int)tm.size();
   *nmembers = (int)t.size();
-  *total_tiles = tiles;
+  *total_tiles = tiles + b->pipe_tiles;
   if (t.empty()) return RLB_OK;
+  if (b->pipe_tiles > b->pipe_tm_capacity) {
+    if (b->d_pipe_tm) cudaFree(b->d_pipe_tm);
+    b->d_pipe_tm = nullptr;
+    const int cap = std::max<int>(b->pipe_tiles, 2 * b->pipe_tm_capacity);
+    cudaError_t e = cudaMalloc((void**)&b->d_pipe_tm, (size_t)cap * sizeof(int));
+    if (e != cudaSuccess) {
+      b->pipe_tm_capacity = 0;
+      return bfail(b, RLB_ENOMEM, std::string("pipelined tile table: ") + cudaGetErrorString(e));
+    }
+    b->pipe_tm_capacity = cap;
+    ++b->version;  // a captured graph holds the old table pointer
+  }
+  if (b->pipe_tiles > 0)
+    BATCH_CUDA(b, cudaMemcpyAsync(b->d_pipe_tm, pipe_tm.data(), pipe_tm.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                  b->stream));
   if ((int)t.size() > b->d_capacity) {
     if (b->d_members) cudaFree(b->d_members);
     b->d_members = nullptr;
@@ -168,7 +227,7 @@ static rlb_status upload_table(rlb_batch* b, long nsteps, int* nmembers, int* to
     b->d_capacity = cap;
     ++b->version;  // a captured graph holds the old table pointer
   }
-  if (tiles > b->tm_capacity) {
+  if (tiles > 0 && tiles > b->tm_capacity) {
     if (b->d_tile_member) cudaFree(b->d_tile_member);
     b->d_tile_member = nullptr;
     const int cap = std::max<int>(tiles, 2 * b->tm_capacity);
@@ -182,8 +241,9 @@ static rlb_status upload_table(rlb_batch* b, long nsteps, int* nmembers, int* to
   }
   BATCH_CUDA(b, cudaMemcpyAsync(b->d_members, t.data(), t.size() * sizeof(BatchMember), cudaMemcpyHostToDevice,
                                 b->stream));
-  BATCH_CUDA(b, cudaMemcpyAsync(b->d_tile_member, tm.data(), tm.size() * sizeof(int), cudaMemcpyHostToDevice,
-                                b->stream));
+  if (tiles > 0)
+    BATCH_CUDA(b, cudaMemcpyAsync(b->d_tile_member, tm.data(), tm.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                  b->stream));
   BATCH_CUDA(b, cudaStreamSynchronize(b->stream));  // the host vector goes away
   return RLB_OK;
 }
@@ -204,18 +264,36 @@ static rlb_status ensure_counters(rlb_batch* b, long nsteps) {
 
 static int grid_of(rlb_batch* b, int variant) { return b->sms * b->launch->batch_blocks_per_sm(variant); }
 
+// One time step (launch index k) of the uploaded table: the pipelined kernel over its tiles, then
+// the register kernels (row tiles, shell tiles) over the other members' tiles.
+static rlb_status enqueue_step(rlb_batch* b, int k, int variant, int* counters) {
+  cudaError_t e = cudaSuccess;
+  if (b->pipe_tiles > 0) {
+    const PipeParams pp{b->lay.producers, b->pipe_tiles, b->lay.nstage, b->lay.groups};
+    const int grid = std::min(b->sms * b->lay.ctas_per_sm, b->pipe_tiles);
+    e = b->launch->pipe_batch_step(b->d_members, b->d_pipe_tm, k, pp, b->pipe_timeout, b->lay.tx, b->pipe_walls, grid,
+                                   b->lay.threads, b->lay.smem, b->stream);
+    ++b->launches;
+    if (e != cudaSuccess) return bfail(b, RLB_ECUDA, std::string("batched pipelined step: ") + cudaGetErrorString(e));
+  }
+  if (b->row_tiles + b->shell_tiles > 0) {
+    const int rv = variant < kNumRegVariants ? variant : reg_fallback(b);
+    e = b->launch->batch_step(b->d_members, b->d_tile_member, b->row_tiles, b->shell_tiles, k, counters, rv, b->walls,
+                              grid_of(b, rv), b->stream);
+    b->launches += (b->row_tiles > 0) + (b->shell_tiles > 0);
+    if (e != cudaSuccess) return bfail(b, RLB_ECUDA, std::string("batched step: ") + cudaGetErrorString(e));
+  }
+  return RLB_OK;
+}
+
 // Enqueue nsteps launches (launch index 0..nsteps-1) directly on the stream.
 static rlb_status enqueue_run(rlb_batch* b, long nsteps, int nmem, int tiles, int variant) {
   (void)nmem;
   (void)tiles;
   BATCH_CUDA(b, cudaMemsetAsync(b->d_counters, 0, (size_t)(2 * nsteps) * sizeof(int), b->stream));
-  const int grid = grid_of(b, variant);
   for (long k = 0; k < nsteps; ++k) {
-    cudaError_t e =
-        b->launch->batch_step(b->d_members, b->d_tile_member, b->row_tiles, b->shell_tiles, (int)k, b->d_counters,
-                              variant, b->walls, grid, b->stream);
-    b->launches += (b->row_tiles > 0) + (b->shell_tiles > 0);
-    if (e != cudaSuccess) return bfail(b, RLB_ECUDA, std::string("batched step: ") + cudaGetErrorString(e));
+    const rlb_status st = enqueue_step(b, (int)k, variant, b->d_counters);
+    if (st != RLB_OK) return st;
   }
   return RLB_OK;
 }
@@ -230,7 +308,7 @@ extern "C" rlb_status rlb_batch_run(rlb_batch* b, long nsteps, int use_graph, in
   if (nsteps > 0) {
     rlb_status st = ensure_counters(b, 2 * nsteps);
     if (st != RLB_OK) return st;
-    st = upload_table(b, nsteps, &nmem, &tiles);
+    st = upload_table(b, nsteps, b->variant, &nmem, &tiles);
     if (st != RLB_OK) return st;
   }
   if (nmem > 0) {
@@ -240,7 +318,8 @@ extern "C" rlb_status rlb_batch_run(rlb_batch* b, long nsteps, int use_graph, in
       // members' row and shell tile counts stay the same
       GraphCache& gc = b->graph;
       if (!gc.exec || gc.nsteps != nsteps || gc.version != b->version || gc.variant != b->variant ||
-          gc.nmembers != nmem || gc.tiles != tiles || gc.row_tiles != b->row_tiles || gc.walls != b->walls) {
+          gc.nmembers != nmem || gc.tiles != tiles || gc.row_tiles != b->row_tiles || gc.walls != b->walls ||
+          gc.pipe_tiles != b->pipe_tiles || gc.pipe_walls != b->pipe_walls) {
         if (b->graph.exec) cudaGraphExecDestroy(b->graph.exec);
         b->graph.exec = nullptr;
         cudaStream_t cs;
@@ -270,9 +349,11 @@ extern "C" rlb_status rlb_batch_run(rlb_batch* b, long nsteps, int use_graph, in
         gc.tiles = tiles;
         gc.row_tiles = b->row_tiles;
         gc.walls = b->walls;
+        gc.pipe_tiles = b->pipe_tiles;
+        gc.pipe_walls = b->pipe_walls;
       }
       BATCH_CUDA(b, cudaGraphLaunch(b->graph.exec, b->stream));
-      b->launches += nsteps * ((b->row_tiles > 0) + (b->shell_tiles > 0));
+      b->launches += nsteps * ((b->row_tiles > 0) + (b->shell_tiles > 0) + (b->pipe_tiles > 0));
     } else {
       rlb_status st = enqueue_run(b, nsteps, nmem, tiles, b->variant);
       if (st != RLB_OK) return st;
@@ -301,43 +382,40 @@ extern "C" rlb_status rlb_batch_autotune(rlb_batch* b, int reps, int* variant, d
   for (const Member& m : b->members)
     if (m.ctx && m.ctx->have_prev)
       return bfail(b, RLB_ESTATE, "rlb_batch_autotune: only while no member has taken a step");
-  int nmem = 0, tiles = 0;
   rlb_status st = ensure_counters(b, 2 * (reps + 1));
   if (st != RLB_OK) return st;
-  st = upload_table(b, 1, &nmem, &tiles);  // steps_left = 1: every launch redoes launch 0
-  if (st != RLB_OK) return st;
   double t[RLB_MAX_VARIANTS] = {0};
-  if (nmem > 0) {
-    cudaEvent_t e0, e1;
-    BATCH_CUDA(b, cudaEventCreate(&e0));
-    BATCH_CUDA(b, cudaEventCreate(&e1));
-    double best = 1e300;
-    int choice = b->variant;
-    for (int v = 0; v < b->launch->step_variants; ++v) {
-      const int grid = grid_of(b, v);
-      BATCH_CUDA(b, cudaMemsetAsync(b->d_counters, 0, (size_t)(2 * (reps + 1)) * sizeof(int), b->stream));
-      for (int r = 0; r <= reps; ++r) {
-        if (r == 1) BATCH_CUDA(b, cudaEventRecord(e0, b->stream));
-        // every repetition is launch 0 of the same run: the same next state into the spare buffers
-        cudaError_t e =
-            b->launch->batch_step(b->d_members, b->d_tile_member, b->row_tiles, b->shell_tiles, 0,
-                                  b->d_counters + 2 * r, v, b->walls, grid, b->stream);
-        if (e != cudaSuccess) return bfail(b, RLB_ECUDA, std::string("batched step: ") + cudaGetErrorString(e));
-      }
-      BATCH_CUDA(b, cudaEventRecord(e1, b->stream));
-      BATCH_CUDA(b, cudaEventSynchronize(e1));
-      float msv = 0.f;
-      BATCH_CUDA(b, cudaEventElapsedTime(&msv, e0, e1));
-      t[v] = msv / reps;
-      if (t[v] < best) {
-        best = t[v];
-        choice = v;
-      }
+  cudaEvent_t e0, e1;
+  BATCH_CUDA(b, cudaEventCreate(&e0));
+  BATCH_CUDA(b, cudaEventCreate(&e1));
+  double best = 1e300;
+  int choice = b->variant;
+  for (int v = 0; v < kNumVariantsTotal && v < RLB_MAX_VARIANTS; ++v) {
+    if (!variant_exists(b, v)) continue;
+    int nmem = 0, tiles = 0;
+    st = upload_table(b, 1, v, &nmem, &tiles);  // steps_left = 1: every launch redoes launch 0
+    if (st != RLB_OK) return st;
+    if (nmem == 0) break;
+    BATCH_CUDA(b, cudaMemsetAsync(b->d_counters, 0, (size_t)(2 * (reps + 1)) * sizeof(int), b->stream));
+    for (int r = 0; r <= reps; ++r) {
+      if (r == 1) BATCH_CUDA(b, cudaEventRecord(e0, b->stream));
+      // every repetition is launch 0 of the same run: the same next state into the spare buffers
+      st = enqueue_step(b, 0, v, b->d_counters + 2 * r);
+      if (st != RLB_OK) return st;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    b->variant = choice;
+    BATCH_CUDA(b, cudaEventRecord(e1, b->stream));
+    BATCH_CUDA(b, cudaEventSynchronize(e1));
+    float msv = 0.f;
+    BATCH_CUDA(b, cudaEventElapsedTime(&msv, e0, e1));
+    t[v] = msv / reps;
+    if (t[v] < best) {
+      best = t[v];
+      choice = v;
+    }
   }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->variant = choice;
   if (variant) *variant = b->variant;
   if (ms)
     for (int v = 0; v < RLB_MAX_VARIANTS; ++v) ms[v] = t[v];
@@ -346,8 +424,7 @@ extern "C" rlb_status rlb_batch_autotune(rlb_batch* b, int reps, int* variant, d
 
 extern "C" rlb_status rlb_batch_set_variant(rlb_batch* b, int variant) {
   if (!b) return RLB_EINVAL;
-  if (variant < 0 || variant >= b->launch->step_variants)
-    return bfail(b, RLB_EINVAL, "rlb_batch_set_variant: no such variant");
+  if (!variant_exists(b, variant)) return bfail(b, RLB_EINVAL, "rlb_batch_set_variant: no such variant");
   b->variant = variant;
   return RLB_OK;
 }
@@ -362,6 +439,7 @@ extern "C" rlb_status rlb_batch_destroy(rlb_batch* b) {
   if (b->graph.exec) cudaGraphExecDestroy(b->graph.exec);
   if (b->d_members) cudaFree(b->d_members);
   if (b->d_tile_member) cudaFree(b->d_tile_member);
+  if (b->d_pipe_tm) cudaFree(b->d_pipe_tm);
   if (b->d_counters) cudaFree(b->d_counters);
   delete b;
   return RLB_OK;

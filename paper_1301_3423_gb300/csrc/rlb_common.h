@@ -74,15 +74,13 @@ enum : int { kPeriodic = 0, kCopyOut = 1, kBounceBack = 2 };
 // device-side waits that ran out, cells with non-finite moments (found by the fields kernel)
 enum : int { kStatusNonconv = 0, kStatusBadInit = 1, kStatusTimeout = 2, kStatusNan = 3, kStatusWords = 4 };
 
-// Launch shape of a pipelined step (k_step_pipe): tiles are TX-cell segments of the lattice rows,
-// tile t = row * segs + seg, block b takes tiles b, b + grid, ...
+// Launch shape of a pipelined step (k_step_pipe, k_step_pipe_batch): tiles are TX-cell segments of
+// the lattice rows, tile t = row * ceil(nx / TX) + seg; block b takes tiles b, b + grid, ...
 struct PipeParams {
   int producers;  // producer warps per block
-  int ntiles;     // segs * ny * nz
-  int segs;       // tiles per row, ceil(nx / TX)
+  int ntiles;     // tiles of the launch: ceil(nx / TX) * ny * nz per lattice
   int nstage;     // shared-memory stages per block (<= 16)
-  int groups;     // consumer groups per block (TX / 32 warps each)
-  int xperiodic;  // x is periodic: the producer resolves the wrap with split copies
+  int groups;     // consumer groups per block (TX / 32 warps each, twice that for float storage)
 };
 
 // One lattice of a batched step (see k_step_batch).
@@ -94,6 +92,7 @@ struct BatchMember {
   int steps_left;     // launches with index >= steps_left leave this member alone
   int row_tile_begin;    // first of its row tiles (4 row-kernel warps each) in the row queue
   int shell_tile_begin;  // first of its shell tiles (kStepThreads shell cells each) in the shell queue
+  int pipe_tile_begin;   // first of its tiles in the pipelined kernel's tile list (k_step_pipe_batch)
 };
 
 }  // namespace rlb

@@ -79,12 +79,18 @@ cudaError_t pipe_step(const void* src, void* dst, const StepParams& p, const Pip
   return RLB_PFN(pipe, 64)(src, dst, p, pp, status, grid, threads, smem, s);
 }
 
+cudaError_t pipe_batch_step(const BatchMember* m, const int* tm, int launch, const PipeParams& pp, int* timeout, int tx,
+                            int walls, int grid, int threads, int smem, cudaStream_t s) {
+  if (tx == 128) return RLB_PFN(pipe_batch, 128)(m, tm, launch, pp, timeout, walls, grid, threads, smem, s);
+  return RLB_PFN(pipe_batch, 64)(m, tm, launch, pp, timeout, walls, grid, threads, smem, s);
+}
+
 }  // namespace
 
 #define RLB_CAT_(a, b, c, d) a##b##c##d
 #define RLB_NAME(o, s) RLB_CAT_(launchers_o, o, _s, s)
 extern const Launchers RLB_NAME(RLB_INST_ORDER, RLB_INST_STORAGE) = {
-    step, fields, init, convert_pops, inst::kVariants, batch_step, batch_blocks_per_sm, pipe_step};
+    step, fields, init, convert_pops, inst::kVariants, batch_step, batch_blocks_per_sm, pipe_step, pipe_batch_step};
 
 #if RLB_INST_ORDER == 3 && RLB_INST_STORAGE == 0
 // Second pass of the conserved-density sums: one block adds the per-block partials in a fixed

@@ -28,7 +28,32 @@ cudaError_t launch_pipe(const void* src, void* dst, const StepParams& p, const P
   kern<<<grid, threads, smem, s>>>((const T*)src, (T*)dst, p, pp, status);
   return cudaGetLastError();
 }
+template <bool W>
+cudaError_t launch_pipe_batch(const BatchMember* m, const int* tm, int launch, const PipeParams& pp, int* timeout,
+                              int grid, int threads, int smem, cudaStream_t s) {
+  auto kern = k_step_pipe_batch<L, S, RLB_INST_TX, W>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  kern<<<grid, threads, smem, s>>>(m, tm, launch, pp, timeout);
+  return cudaGetLastError();
+}
 }  // namespace
+
+// One time step of every active batch member on the pipelined kernel (walls: some member has
+// bounce-back walls).
+cudaError_t RLB_PFN(pipe_batch, RLB_INST_TX)(const BatchMember* m, const int* tm, int launch, const PipeParams& pp,
+                                             int* timeout, int walls, int grid, int threads, int smem,
+                                             cudaStream_t s) {
+  if (walls) return launch_pipe_batch<true>(m, tm, launch, pp, timeout, grid, threads, smem, s);
+  return launch_pipe_batch<false>(m, tm, launch, pp, timeout, grid, threads, smem, s);
+}
 
 // One time step of the whole lattice in one launch, compiled with the bounce-back patch only for
 // lattices that have walls.

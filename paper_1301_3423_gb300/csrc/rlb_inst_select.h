@@ -46,7 +46,9 @@ constexpr int kVariants = kFloat ? kNumVariants : 1;
 #define RLB_PFN(fn, tx) RLB_CAT7(fn, _o, RLB_INST_ORDER, _s, RLB_INST_STORAGE, _x, tx)
 #define RLB_DECLARE_PIPE(tx)                                                                                   \
   cudaError_t RLB_PFN(pipe, tx)(const void* src, void* dst, const StepParams& p, const PipeParams& pp, int* status, \
-                                int grid, int threads, int smem, cudaStream_t s);
+                                int grid, int threads, int smem, cudaStream_t s);                                 \
+  cudaError_t RLB_PFN(pipe_batch, tx)(const BatchMember* m, const int* tm, int launch, const PipeParams& pp,        \
+                                      int* timeout, int walls, int grid, int threads, int smem, cudaStream_t s);
 RLB_DECLARE_PIPE(64)
 RLB_DECLARE_PIPE(128)
 #undef RLB_DECLARE_PIPE

@@ -3,6 +3,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "rlb_common.h"
+
 namespace rlb {
 struct StepParams;
 struct PipeParams;
@@ -25,10 +27,46 @@ struct Launchers {
                             int launch_index, int* counters, int variant, int walls, int grid, cudaStream_t s);
   // resident blocks per SM of the batched step for a variant
   int (*batch_blocks_per_sm)(int variant);
-  // one time step of the pipelined kernel with tile width tx (32 or 64)
+  // one time step of the pipelined kernel with tile width tx (64 or 128)
   cudaError_t (*pipe_step)(const void* src, void* dst, const StepParams& p, const PipeParams& pp, int* status, int tx,
                            int grid, int threads, int smem, cudaStream_t s);
+  // one time step of the batched pipelined kernel (launch index `launch`) over the members' tiles;
+  // walls != 0 selects the kernel with the bounce-back patch
+  cudaError_t (*pipe_batch_step)(const BatchMember* members, const int* tile_member, int launch, const PipeParams& pp,
+                                 int* timeout, int tx, int walls, int grid, int threads, int smem, cudaStream_t s);
 };
+
+// Block layout of pipelined variant v (>= kNumRegVariants) for q populations of `elem` bytes:
+// stages (the largest multiple of the consumer-group count that fits the shared memory of one
+// block, at least two per group), groups, threads and shared-memory bytes.  False if the variant
+// does not exist for this storage.
+struct PipeLayout {
+  int tx, nstage, groups, producers, threads, smem, ctas_per_sm;
+};
+
+inline bool pipe_layout(int v, int q, int elem, int smem_per_sm, int smem_optin, PipeLayout* out) {
+  if (v < kNumRegVariants || v >= kNumVariantsTotal) return false;
+  const PipeConfig& cf = kPipeConfigs[v - kNumRegVariants];
+  const int A = 16 / elem;
+  const long long stage = (long long)q * (cf.tx + A) * elem;
+  long long budget = smem_per_sm / cf.ctas_per_sm - 1024;
+  if (budget > smem_optin) budget = smem_optin;
+  const bool split = elem == 4;  // float storage: two consumer warps per cell
+  const int wpt = cf.tx / 32 * (split ? 2 : 1);
+  const int groups = cf.cons_warps / wpt;
+  if (groups < 1 || cf.cons_warps % wpt != 0 || cf.producers < 1 || cf.producers > q) return false;
+  if (cf.producers > kPipeMaxProducerWarps || cf.cons_warps > kPipeMaxConsumerWarps ||
+      cf.cons_warps + cf.producers > kPipeMaxWarps)
+    return false;
+  const long long xchg = split ? (long long)cf.cons_warps / 2 * kPipeXchgBytesPerPair : 0;
+  long long fit = (budget - kPipeHeaderBytes - xchg) / stage;
+  if (fit > kPipeMaxStages) fit = kPipeMaxStages;
+  const int nstage = (int)(fit / groups * groups);
+  if (nstage < 2 * groups) return false;
+  if (out) *out = PipeLayout{cf.tx, nstage, groups, cf.producers, (cf.cons_warps + cf.producers) * 32,
+                             (int)(kPipeHeaderBytes + nstage * stage + xchg), cf.ctas_per_sm};
+  return true;
+}
 
 #define RLB_DECLARE_LAUNCHERS(ORDER, STORAGE) extern const Launchers launchers_o##ORDER##_s##STORAGE;
 RLB_DECLARE_LAUNCHERS(3, 0)

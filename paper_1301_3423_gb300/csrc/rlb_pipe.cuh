@@ -179,11 +179,13 @@ __device__ __forceinline__ int pipe_src_row(int s, int n, int bc) {
   return min(max(s, 0), n - 1);
 }
 
-template <class L, class S, int TX, bool WALLS>
-__global__ void __launch_bounds__(kPipeMaxThreads, 1)
-    k_step_pipe(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
-                const __grid_constant__ StepParams p, const __grid_constant__ PipeParams pp,
-                int* __restrict__ status) {
+// The pipeline of one launch over tiles t = blockIdx.x + k gridDim.x, k = 0, 1, ... < pp.ntiles.
+// `tiles` maps a tile to its lattice: tiles.at(t) gives a TileRef (the lattice's parameters,
+// buffers and status words, the tile's index within that lattice, and whether the lattice steps in
+// this launch); a tile of a lattice that does not step still passes through its stage (no copies,
+// no stores) so that every producer and consumer keeps the stage order.
+template <class L, class S, int TX, bool WALLS, class Tiles>
+__device__ __forceinline__ void pipe_body(const PipeParams& pp, const Tiles& tiles) {
   using T = typename S::T;
   using A = typename S::A;
   using Sh = PipeShape<S, TX>;
@@ -238,11 +240,17 @@ __global__ void __launch_bounds__(kPipeMaxThreads, 1)
         ok = false;
         break;
       }
-      if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)(mine * Sh::ROW_BYTES));
+      const auto tr = tiles.at(t);
+      const StepParams& p = tr.p;
+      if (lane == 0) mbar_arrive_expect_tx(&full[s], tr.active ? (uint32_t)(mine * Sh::ROW_BYTES) : 0u);
       __syncwarp();
-      const int seg = (int)(t % pp.segs), row = (int)(t / pp.segs);
+      if (!tr.active) continue;
+      const T* __restrict__ src = tr.src;
+      const int segs = (p.nx + TX - 1) / TX;
+      const int seg = tr.lt % segs, row = tr.lt / segs;
       const int y = row % p.ny, z = row / p.ny;
       const int x0 = seg * TX;
+      const bool xperiodic = p.bc[0] == kPeriodic;
       T* const st = stage0 + (size_t)s * kStageElems;
       for (int i = lane * P + pw; i < L::Q; i += 32 * P) {
         const char4 v = sv[i];
@@ -251,7 +259,7 @@ __global__ void __launch_bounds__(kPipeMaxThreads, 1)
         const T* rowp = src + (long long)i * p.cells + ((long long)zs * p.ny + ys) * p.nx;
         const int xs = (x0 - v.x) & ~(AL - 1);  // round down to a granule (two's complement: floor)
         T* d = st + i * BX;
-        if (pp.xperiodic && (xs < 0 || xs + BX > p.nx)) {
+        if (xperiodic && (xs < 0 || xs + BX > p.nx)) {
           // split [xs, xs + BX) at multiples of nx; each piece is whole granules of one period
           int a = xs;
           const int e = xs + BX;
@@ -269,7 +277,7 @@ __global__ void __launch_bounds__(kPipeMaxThreads, 1)
       }
     }
     if (!ok) {
-      if (lane == 0) atomicAdd(&status[kStatusTimeout], 1);
+      if (lane == 0) atomicAdd(tiles.timeout_word(), 1);
       // let the copies already issued land before the block's shared memory goes away (each stage's
       // latest use among the last nstage tiles)
       for (int j = max(0, k - pp.nstage); j < k; ++j) mbar_wait(&full[j % pp.nstage], (uint32_t)(j / pp.nstage) & 1u);
@@ -293,10 +301,21 @@ __global__ void __launch_bounds__(kPipeMaxThreads, 1)
     if (t >= pp.ntiles) break;
     const int s = k % pp.nstage;
     if (!mbar_wait(&full[s], (uint32_t)(k / pp.nstage) & 1u)) {
-      if (lane == 0) atomicAdd(&status[kStatusTimeout], 1);
+      if (lane == 0) atomicAdd(tiles.timeout_word(), 1);
       return;
     }
-    const int seg = (int)(t % pp.segs), row = (int)(t / pp.segs);
+    const auto tr = tiles.at(t);
+    if (!tr.active) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+      continue;
+    }
+    const StepParams& p = tr.p;
+    const T* __restrict__ src = tr.src;
+    T* __restrict__ dst = tr.dst;
+    int* __restrict__ status = tr.status;
+    const int segs = (p.nx + TX - 1) / TX;
+    const int seg = tr.lt % segs, row = tr.lt / segs;
     Cell cl;
     cl.y = row % p.ny;
     cl.z = row / p.ny;
@@ -308,7 +327,8 @@ __global__ void __launch_bounds__(kPipeMaxThreads, 1)
     T* const lb = stage0 + (size_t)s * kStageElems + part * 32 + lane;
 
     // patch what the copies could not express (warp-uniform test), for the populations this warp reads
-    bool patch = !pp.xperiodic && (x0 < L::VMAX_X || x0 + TX - 1 + L::VMAX_X >= p.nx);
+    const bool xperiodic = p.bc[0] == kPeriodic;
+    bool patch = !xperiodic && (x0 < L::VMAX_X || x0 + TX - 1 + L::VMAX_X >= p.nx);
     if constexpr (WALLS)
       patch = patch || (p.bc[1] == kBounceBack && (cl.y < L::VMAX_Y || cl.y >= p.ny - L::VMAX_Y)) ||
               (p.bc[2] == kBounceBack && (cl.z < L::VMAX_Z || cl.z >= p.nz - L::VMAX_Z));
@@ -321,7 +341,7 @@ __global__ void __launch_bounds__(kPipeMaxThreads, 1)
         if (SPLIT && ih != half) return;
         bool need = false;
         if constexpr (WALLS) need = p.has_wall && beyond_wall<L, i>(cl, p);
-        if constexpr (vx != 0) need = need || (!pp.xperiodic && (unsigned)(cl.x - vx) >= (unsigned)p.nx);
+        if constexpr (vx != 0) need = need || (!xperiodic && (unsigned)(cl.x - vx) >= (unsigned)p.nx);
         if (need) lb[i * BX + r] = src[pull_index<L, i, true, WALLS>(cl, p)];
       });
       fence_proxy_async_smem();
@@ -390,6 +410,69 @@ __global__ void __launch_bounds__(kPipeMaxThreads, 1)
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
   }
+}
+
+
+// A tile and the lattice it belongs to.
+template <class T>
+struct TileRef {
+  const StepParams& p;
+  const T* src;
+  T* dst;
+  int* status;
+  int lt;       // the tile's index within its lattice: row * segs + seg
+  bool active;  // the lattice steps in this launch
+};
+
+// One lattice: tile t is the lattice's tile t.
+template <class T>
+struct SoloTiles {
+  const StepParams& p;
+  const T* src;
+  T* dst;
+  int* status;
+  __device__ __forceinline__ TileRef<T> at(long long t) const { return TileRef<T>{p, src, dst, status, (int)t, true}; }
+  __device__ __forceinline__ int* timeout_word() const { return status + kStatusTimeout; }
+};
+
+// Many lattices (batch members): tile t belongs to member tile_member[t], whose tiles start at its
+// pipe_tile_begin; the member reads buf[(parity0 + launch) & 1] and writes the other buffer, and
+// steps only while launch < steps_left.
+template <class T>
+struct BatchTiles {
+  const BatchMember* members;
+  const int* tile_member;
+  int launch;
+  int* timeout;
+  __device__ __forceinline__ TileRef<T> at(long long t) const {
+    const int mi = __ldg(&tile_member[t]);
+    const BatchMember& m = members[mi];
+    const int par = (m.parity0 + launch) & 1;
+    return TileRef<T>{m.p, static_cast<const T*>(m.buf[par]), static_cast<T*>(m.buf[par ^ 1]), m.status,
+                      (int)(t - m.pipe_tile_begin), launch < m.steps_left};
+  }
+  __device__ __forceinline__ int* timeout_word() const { return timeout; }
+};
+
+// One time step of one lattice.
+template <class L, class S, int TX, bool WALLS>
+__global__ void __launch_bounds__(kPipeMaxThreads, 1)
+    k_step_pipe(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
+                const __grid_constant__ StepParams p, const __grid_constant__ PipeParams pp,
+                int* __restrict__ status) {
+  using T = typename S::T;
+  pipe_body<L, S, TX, WALLS>(pp, SoloTiles<T>{p, src, dst, status});
+}
+
+// One time step of every batch member with steps left (launch index `launch`), persistent over the
+// members' tiles.  A member's result is bitwise that of k_step_pipe on it alone.  Waits that run
+// out are counted in *timeout (the first member's status words).
+template <class L, class S, int TX, bool WALLS>
+__global__ void __launch_bounds__(kPipeMaxThreads, 1)
+    k_step_pipe_batch(const BatchMember* __restrict__ members, const int* __restrict__ tile_member, int launch,
+                      const __grid_constant__ PipeParams pp, int* __restrict__ timeout) {
+  using T = typename S::T;
+  pipe_body<L, S, TX, WALLS>(pp, BatchTiles<T>{members, tile_member, launch, timeout});
 }
 
 }  // namespace rlb

@@ -415,8 +415,8 @@ class Batch:
         v = ctypes.c_int()
         ms = (ctypes.c_double * MAX_VARIANTS)()
         self._check(self._lib.rlb_batch_autotune(self._h, int(reps), ctypes.byref(v), ms))
-        n = sum(1 for x in ms if x > 0)
-        return v.value, list(ms)[:max(n, 1)]
+        n = max([i + 1 for i, x in enumerate(ms) if x > 0] or [1])
+        return v.value, list(ms)[:n]
 
     def set_variant(self, v):
         self._check(self._lib.rlb_batch_set_variant(self._h, int(v)))
