@@ -1007,89 +1007,6 @@ __global__ void __launch_bounds__(kStepThreads, StepShape<S, VARIANT>::kMinBlock
 }
 
 // ---------------------------------------------------------------------------------------------
-// fields and conserved densities of one time level (double arithmetic; for float storages the
-// Landau solve starts from the float solution and stops at 1e-12 U0)
-//   PULL = true : the pre-collision populations pulled from the previous state (GENERAL: modulo
-//                 wrap, for periodic axes shorter than the stencil reach)
-//   PULL = false: the stored populations of each cell
-// fields[k][cell], k = n, eps, U0, U1, U2, U3; partial[block][5] = block sums of
-// N^0, T^00, T^0x, T^0y, T^0z, reduced by warp shuffles in a fixed order.
-// ---------------------------------------------------------------------------------------------
-template <class L, class S, bool PULL, bool GENERAL>
-__global__ void __launch_bounds__(kMomThreads) k_fields(const typename S::T* __restrict__ src,
-                                                        const __grid_constant__ StepParams p,
-                                                        double* __restrict__ fields,
-                                                        double* __restrict__ partial,
-                                                        int* __restrict__ status) {
-  const int gid = blockIdx.x * kMomThreads + threadIdx.x;
-  const bool valid = gid < p.cells;
-  const Cell cl = make_cell(valid ? gid : p.cells - 1, p);
-  auto index = [&](auto I) -> long long {
-    constexpr int i = decltype(I)::value;
-    return PULL ? pull_index<L, i, GENERAL, true>(cl, p) : (long long)i * p.cells + cl.c;
-  };
-  Mom<double> m;
-  Landau<double> lw;
-  if constexpr (std::is_same<typename S::A, double>::value) {
-    m = moments<L, double>([&](auto I) -> double { return src[index(I)]; });
-    lw = landau<double, 200>(m);
-  } else {
-    // float populations: the per-cell moments in float, as the step takes them (paired sums per
-    // direction; deviations for half storage); Landau matching from the float solution refined in
-    // double to 1e-12 U0 (float moments carry no more); the cross-cell sums below in double
-    constexpr bool DEV = std::is_same<S, StoreF16Dev>::value;
-    auto getf = [&](auto I) -> float {
-      constexpr int i = decltype(I)::value;
-      if constexpr (DEV) return S::template load_dev<L, i>(src + index(I), p);
-      else return (float)src[index(I)];
-    };
-    auto get2 = [&](auto I) -> float2 {
-      constexpr int i = decltype(I)::value;
-      return make_float2(getf(ic<i>{}), getf(ic<i + 1>{}));
-    };
-    const Mom<float> mf = moments_f2<L, DEV>(get2, p.half_nref);
-    m = convert<float, double>(mf);
-    const Landau<float> lf = landau<float, 8>(mf);
-    if (lf.ok) lw = landau_from<double, 200>(m, (double)lf.U0, (double)lf.Ux, (double)lf.Uy, (double)lf.Uz, 1e-12);
-    else lw = landau<double, 200>(m);
-  }
-  if (valid) {
-    const double nan = __longlong_as_double(0x7ff8000000000000ll);
-    fields[0 * (long long)p.cells + cl.c] = lw.ok ? lw.n : nan;
-    fields[1 * (long long)p.cells + cl.c] = lw.ok ? lw.eps : nan;
-    fields[2 * (long long)p.cells + cl.c] = lw.ok ? lw.U0 : nan;
-    fields[3 * (long long)p.cells + cl.c] = lw.ok ? lw.Ux : nan;
-    fields[4 * (long long)p.cells + cl.c] = lw.ok ? lw.Uy : nan;
-    fields[5 * (long long)p.cells + cl.c] = lw.ok ? lw.Uz : nan;
-    // non-finite populations show as non-finite moments; any other cell without a frame is a
-    // Landau failure
-    const bool finite = isfinite(m.N0) && isfinite(m.Nx) && isfinite(m.Ny) && isfinite(m.Nz) && isfinite(m.T00) &&
-                        isfinite(m.T0x) && isfinite(m.T0y) && isfinite(m.T0z) && isfinite(m.Txx) &&
-                        isfinite(m.Tyy) && isfinite(m.Tzz) && isfinite(m.Txy) && isfinite(m.Txz) && isfinite(m.Tyz);
-    if (!finite) atomicAdd(&status[kStatusNan], 1);
-    else if (!lw.ok) atomicAdd(&status[kStatusNonconv], 1);
-  }
-  double d[5] = {valid ? m.N0 : 0.0, valid ? m.T00 : 0.0, valid ? m.T0x : 0.0, valid ? m.T0y : 0.0,
-                 valid ? m.T0z : 0.0};
-#pragma unroll
-  for (int k = 0; k < 5; ++k)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) d[k] += __shfl_down_sync(0xffffffffu, d[k], o);
-  __shared__ double ws[kMomThreads / 32][5];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < 5; ++k) ws[warp][k] = d[k];
-  __syncthreads();
-  if (threadIdx.x < 5) {
-    double s = 0.0;
-#pragma unroll
-    for (int w = 0; w < kMomThreads / 32; ++w) s += ws[w][threadIdx.x];
-    partial[(long long)blockIdx.x * 5 + threadIdx.x] = s;
-  }
-}
-
-// ---------------------------------------------------------------------------------------------
 // float-float arithmetic: a value as the unevaluated sum hi + lo of two floats (|lo| <= ulp(hi)/2),
 // built from the error-free transformations of Dekker and Knuth (two-sum; two-product by FMA).
 // About 44 bits of significand, at float-pipe speed.
@@ -1140,6 +1057,171 @@ __device__ __forceinline__ float ff_horner3(FF t, FF a, FF b, FF c, FF d) {
   r = ff_add(ff_mul(r, t), b);
   r = ff_add(ff_mul(r, t), a);
   return r.hi + r.lo;
+}
+
+// a float-float constant from a compile-time double
+struct FFC {
+  float hi, lo;
+};
+__host__ __device__ constexpr FFC ffc(double x) { return FFC{(float)x, (float)(x - (double)(float)x)}; }
+
+// a times the float b, in float-float
+__device__ __forceinline__ FF ff_mulf(FFC a, float b) {
+  const float p = a.hi * b;
+  return fast_two_sum(p, fmaf(a.hi, b, -p) + a.lo * b);
+}
+
+__device__ __forceinline__ FF ff_mulc(FF a, FFC b) {
+  const float p = a.hi * b.hi;
+  return fast_two_sum(p, fmaf(a.hi, b.hi, -p) + fmaf(a.hi, b.lo, a.lo * b.hi));
+}
+
+__device__ __forceinline__ FF ff_sub(FF a, FF b) { return ff_add(a, ff_neg(b)); }
+
+__device__ __forceinline__ double ff_to_double(FF a) { return (double)a.hi + (double)a.lo; }
+
+// The moments of float populations (deviations d_i for half storage, with the weights' own moments
+// times c added), accumulated in float-float: the per-direction sums over energies, then the
+// direction pairs' contributions, each with about 44 bits.  Float sums of the +v and -v directions
+// cancel to a few 1e-6 of T^00 in T^{0a} (the velocity); these stay near float rounding of the
+// populations themselves.  Returned in double, T^zz from the trace identity.
+template <class L, bool DEV, class GetF>
+__device__ __forceinline__ Mom<double> moments_ff(GetF&& getf, double c) {
+  const FF z{0.f, 0.f};
+  FF N0 = z, Nx = z, Ny = z, Nz = z, T00 = z, T0x = z, T0y = z, T0z = z, Txx = z, Tyy = z, Txy = z, Txz = z, Tyz = z;
+  static_for<L::NDP>([&](auto K) {
+    constexpr int k = decltype(K)::value;
+    constexpr int first = L::DP_FIRST[k];
+    constexpr int np = L::DP_NPAIR[k];
+    FF S1p = z, S1m = z, S2p = z, S2m = z;
+    static_for<np>([&](auto J) {
+      constexpr int ip = first + 2 * decltype(J)::value;
+      constexpr double wk = DEV ? L::W[ip] : 1.0;  // mirror partners share the weight
+      constexpr FFC p0 = ffc(wk * L::P0[L::LEV[ip]]);
+      constexpr FFC p02 = ffc(wk * L::P0[L::LEV[ip]] * L::P0[L::LEV[ip]]);
+      const float fa = getf(ic<ip>{}), fb = getf(ic<ip + 1>{});
+      S1p = ff_add(S1p, ff_mulf(p0, fa));
+      S1m = ff_add(S1m, ff_mulf(p0, fb));
+      S2p = ff_add(S2p, ff_mulf(p02, fa));
+      S2m = ff_add(S2m, ff_mulf(p02, fb));
+    });
+    constexpr int vx = L::VX[first], vy = L::VY[first], vz = L::VZ[first];
+    const FF S2 = ff_add(S2p, S2m), D1 = ff_sub(S1p, S1m), D2 = ff_sub(S2p, S2m);
+    N0 = ff_add(N0, ff_add(S1p, S1m));
+    T00 = ff_add(T00, S2);
+    if constexpr (vx != 0) {
+      Nx = ff_add(Nx, ff_mulc(D1, ffc(vx * L::INV_R)));
+      T0x = ff_add(T0x, ff_mulc(D2, ffc(vx * L::INV_R)));
+      Txx = ff_add(Txx, ff_mulc(S2, ffc(vx * vx * L::INV_R2)));
+    }
+    if constexpr (vy != 0) {
+      Ny = ff_add(Ny, ff_mulc(D1, ffc(vy * L::INV_R)));
+      T0y = ff_add(T0y, ff_mulc(D2, ffc(vy * L::INV_R)));
+      Tyy = ff_add(Tyy, ff_mulc(S2, ffc(vy * vy * L::INV_R2)));
+    }
+    if constexpr (vz != 0) {
+      Nz = ff_add(Nz, ff_mulc(D1, ffc(vz * L::INV_R)));
+      T0z = ff_add(T0z, ff_mulc(D2, ffc(vz * L::INV_R)));
+    }
+    if constexpr (vx != 0 && vy != 0) Txy = ff_add(Txy, ff_mulc(S2, ffc(vx * vy * L::INV_R2)));
+    if constexpr (vx != 0 && vz != 0) Txz = ff_add(Txz, ff_mulc(S2, ffc(vx * vz * L::INV_R2)));
+    if constexpr (vy != 0 && vz != 0) Tyz = ff_add(Tyz, ff_mulc(S2, ffc(vy * vz * L::INV_R2)));
+  });
+  Mom<double> m;
+  m.N0 = ff_to_double(N0);
+  m.Nx = ff_to_double(Nx);
+  m.Ny = ff_to_double(Ny);
+  m.Nz = ff_to_double(Nz);
+  m.T00 = ff_to_double(T00);
+  m.T0x = ff_to_double(T0x);
+  m.T0y = ff_to_double(T0y);
+  m.T0z = ff_to_double(T0z);
+  m.Txx = ff_to_double(Txx);
+  m.Tyy = ff_to_double(Tyy);
+  m.Txy = ff_to_double(Txy);
+  m.Txz = ff_to_double(Txz);
+  m.Tyz = ff_to_double(Tyz);
+  if constexpr (DEV) add_rest_sums<L, double>(m, c);
+  m.Tzz = m.T00 - m.Txx - m.Tyy;
+  return m;
+}
+
+// ---------------------------------------------------------------------------------------------
+// fields and conserved densities of one time level (double arithmetic; for float storages the
+// Landau solve starts from the float solution and stops at 1e-12 U0)
+//   PULL = true : the pre-collision populations pulled from the previous state (GENERAL: modulo
+//                 wrap, for periodic axes shorter than the stencil reach)
+//   PULL = false: the stored populations of each cell
+// fields[k][cell], k = n, eps, U0, U1, U2, U3; partial[block][5] = block sums of
+// N^0, T^00, T^0x, T^0y, T^0z, reduced by warp shuffles in a fixed order.
+// ---------------------------------------------------------------------------------------------
+template <class L, class S, bool PULL, bool GENERAL>
+__global__ void __launch_bounds__(kMomThreads) k_fields(const typename S::T* __restrict__ src,
+                                                        const __grid_constant__ StepParams p,
+                                                        double* __restrict__ fields,
+                                                        double* __restrict__ partial,
+                                                        int* __restrict__ status) {
+  const int gid = blockIdx.x * kMomThreads + threadIdx.x;
+  const bool valid = gid < p.cells;
+  const Cell cl = make_cell(valid ? gid : p.cells - 1, p);
+  auto index = [&](auto I) -> long long {
+    constexpr int i = decltype(I)::value;
+    return PULL ? pull_index<L, i, GENERAL, true>(cl, p) : (long long)i * p.cells + cl.c;
+  };
+  Mom<double> m;
+  Landau<double> lw;
+  if constexpr (std::is_same<typename S::A, double>::value) {
+    m = moments<L, double>([&](auto I) -> double { return src[index(I)]; });
+    lw = landau<double, 200>(m);
+  } else {
+    // float populations: the per-cell moments in float-float arithmetic (deviations for half
+    // storage), no double operation per population; Landau matching from the float solution
+    // refined in double to 1e-12 U0; the cross-cell sums below in double
+    constexpr bool DEV = std::is_same<S, StoreF16Dev>::value;
+    auto getf = [&](auto I) -> float {
+      constexpr int i = decltype(I)::value;
+      if constexpr (DEV) return S::template load_dev<L, i>(src + index(I), p);
+      else return (float)src[index(I)];
+    };
+    m = moments_ff<L, DEV>(getf, (double)p.half_nref);
+    const Landau<float> lf = landau<float, 8>(convert<double, float>(m));
+    if (lf.ok) lw = landau_from<double, 200>(m, (double)lf.U0, (double)lf.Ux, (double)lf.Uy, (double)lf.Uz, 1e-12);
+    else lw = landau<double, 200>(m);
+  }
+  if (valid) {
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    fields[0 * (long long)p.cells + cl.c] = lw.ok ? lw.n : nan;
+    fields[1 * (long long)p.cells + cl.c] = lw.ok ? lw.eps : nan;
+    fields[2 * (long long)p.cells + cl.c] = lw.ok ? lw.U0 : nan;
+    fields[3 * (long long)p.cells + cl.c] = lw.ok ? lw.Ux : nan;
+    fields[4 * (long long)p.cells + cl.c] = lw.ok ? lw.Uy : nan;
+    fields[5 * (long long)p.cells + cl.c] = lw.ok ? lw.Uz : nan;
+    // non-finite populations show as non-finite moments; any other cell without a frame is a
+    // Landau failure
+    const bool finite = isfinite(m.N0) && isfinite(m.Nx) && isfinite(m.Ny) && isfinite(m.Nz) && isfinite(m.T00) &&
+                        isfinite(m.T0x) && isfinite(m.T0y) && isfinite(m.T0z) && isfinite(m.Txx) &&
+                        isfinite(m.Tyy) && isfinite(m.Tzz) && isfinite(m.Txy) && isfinite(m.Txz) && isfinite(m.Tyz);
+    if (!finite) atomicAdd(&status[kStatusNan], 1);
+    else if (!lw.ok) atomicAdd(&status[kStatusNonconv], 1);
+  }
+  double d[5] = {valid ? m.N0 : 0.0, valid ? m.T00 : 0.0, valid ? m.T0x : 0.0, valid ? m.T0y : 0.0,
+                 valid ? m.T0z : 0.0};
+#pragma unroll
+  for (int k = 0; k < 5; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d[k] += __shfl_down_sync(0xffffffffu, d[k], o);
+  __shared__ double ws[kMomThreads / 32][5];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < 5; ++k) ws[warp][k] = d[k];
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kMomThreads / 32; ++w) s += ws[w][threadIdx.x];
+    partial[(long long)blockIdx.x * 5 + threadIdx.x] = s;
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
