@@ -46,7 +46,8 @@ typedef enum {
   RLB_ECUDA = 3,    /* a CUDA call failed; the context should be destroyed */
   RLB_ENONCONV = 4, /* Landau matching found no timelike eigenvector in some cell */
   RLB_ENAN = 5,     /* non-finite populations (found by rlb_moments) */
-  RLB_ETIMEOUT = 6, /* a bounded device-side wait of the pipelined step kernel ran out */
+  RLB_ETIMEOUT = 6, /* a bounded device-side wait of the pipelined step kernel ran out; the state
+                       that step produced is not valid (rlb_init or rlb_set_populations restores one) */
   RLB_ESTATE = 7    /* call not valid in the context's current state */
 } rlb_status;
 
@@ -91,6 +92,9 @@ typedef struct {
   int step_variant;   /* -1 = library default, or force a step-kernel variant (see rlb_autotune);
                          a variant that does not exist for the context falls back to the default */
   void* stream;       /* cudaStream_t to enqueue on; NULL = the default stream */
+  int debug_flags;    /* testing only, 0 in normal use.  Bit 0: the pipelined step kernel's producer
+                         warps do nothing, so its consumers' bounded waits (2 s) run out and the next
+                         synchronising call reports RLB_ETIMEOUT; the context stays usable. */
   /* Optional quadrature (Sec. II.C, App. A).  When q > 0 these arrays are compared with the
    * quadrature compiled into the library for this order and must match exactly (RLB_EINVAL
    * otherwise); rlb_quadrature() returns the built-in one. */

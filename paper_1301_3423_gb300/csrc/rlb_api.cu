@@ -255,6 +255,7 @@ extern "C" rlb_status rlb_create(const rlb_params* p, rlb_ctx** out) {
   sp.gamma_thr2 = (float)(p->gamma_thr * p->gamma_thr);
   sp.landau_fp64 = p->landau_fp64 ? 1 : 0;
   sp.half_nref = (float)(0.5 * p->n_ref);
+  sp.debug = p->debug_flags;
   static const Launchers* const table[2][3] = {{&launchers_o2_s0, &launchers_o2_s1, &launchers_o2_s2},
                                                {&launchers_o3_s0, &launchers_o3_s1, &launchers_o3_s2}};
   c->launch = table[p->order == 3 ? 1 : 0][p->storage];
@@ -355,6 +356,10 @@ static rlb_status read_status(rlb_ctx* c) {
   if (st[kStatusNan] > 0) {
     RLB_CUDA(c, cudaMemsetAsync(c->status, 0, kStatusWords * sizeof(int), c->stream));
     return fail(c, RLB_ENAN, std::to_string(st[kStatusNan]) + " cells with non-finite populations");
+  }
+  if (st[kStatusBounds] > 0) {
+    RLB_CUDA(c, cudaMemsetAsync(c->status, 0, kStatusWords * sizeof(int), c->stream));
+    return fail(c, RLB_ECUDA, std::to_string(st[kStatusBounds]) + " pull addresses outside the population buffer");
   }
   if (st[kStatusTimeout] > 0) {
     RLB_CUDA(c, cudaMemsetAsync(c->status, 0, kStatusWords * sizeof(int), c->stream));

@@ -56,6 +56,7 @@ struct StepParams {
   int landau_fp64;
   float half_nref;          // F16DEV: n_ref / 2
   int general;              // a periodic axis is shorter than the stencil reach (modulo wrap)
+  int debug;                // kDebug* bits (testing only; 0 in normal use)
   int has_wall;             // some axis has bounce-back walls (bc == kBounceBack)
   // Interior box: cells whose whole stencil stays inside the lattice, x in [ix0, ix0 + ixn) etc.
   int ix0, ixn, iy0, iyn, iz0, izn;
@@ -71,8 +72,20 @@ struct StepParams {
 enum : int { kPeriodic = 0, kCopyOut = 1, kBounceBack = 2 };
 
 // status words: cell updates without a Landau frame, cells with invalid initial fields, bounded
-// device-side waits that ran out, cells with non-finite moments (found by the fields kernel)
-enum : int { kStatusNonconv = 0, kStatusBadInit = 1, kStatusTimeout = 2, kStatusNan = 3, kStatusWords = 4 };
+// device-side waits that ran out, cells with non-finite moments (found by the fields kernel), pull
+// addresses outside the population buffer and its guard bytes (found and skipped by the pipelined
+// kernel)
+enum : int {
+  kStatusNonconv = 0,
+  kStatusBadInit = 1,
+  kStatusTimeout = 2,
+  kStatusNan = 3,
+  kStatusBounds = 4,
+  kStatusWords = 8
+};
+
+// StepParams::debug bits (testing only)
+enum : int { kDebugStallProducers = 1 };  // the pipelined step's producers do nothing: every wait runs out
 
 // Launch shape of a pipelined step (k_step_pipe, k_step_pipe_batch): tiles are TX-cell segments of
 // the lattice rows, tile t = row * ceil(nx / TX) + seg; block b takes tiles b, b + grid, ...

@@ -1059,88 +1059,58 @@ __device__ __forceinline__ float ff_horner3(FF t, FF a, FF b, FF c, FF d) {
   return r.hi + r.lo;
 }
 
-// a float-float constant from a compile-time double
-struct FFC {
-  float hi, lo;
-};
-__host__ __device__ constexpr FFC ffc(double x) { return FFC{(float)x, (float)(x - (double)(float)x)}; }
-
-// a times the float b, in float-float
-__device__ __forceinline__ FF ff_mulf(FFC a, float b) {
-  const float p = a.hi * b;
-  return fast_two_sum(p, fmaf(a.hi, b, -p) + a.lo * b);
-}
-
-__device__ __forceinline__ FF ff_mulc(FF a, FFC b) {
-  const float p = a.hi * b.hi;
-  return fast_two_sum(p, fmaf(a.hi, b.hi, -p) + fmaf(a.hi, b.lo, a.lo * b.hi));
-}
-
-__device__ __forceinline__ FF ff_sub(FF a, FF b) { return ff_add(a, ff_neg(b)); }
-
-__device__ __forceinline__ double ff_to_double(FF a) { return (double)a.hi + (double)a.lo; }
-
 // The moments of float populations (deviations d_i for half storage, with the weights' own moments
-// times c added), accumulated in float-float: the per-direction sums over energies, then the
-// direction pairs' contributions, each with about 44 bits.  Float sums of the +v and -v directions
-// cancel to a few 1e-6 of T^00 in T^{0a} (the velocity); these stay near float rounding of the
-// populations themselves.  Returned in double, T^zz from the trace identity.
+// times c added) for the fields readout: per direction pair, the sums over energies for +v and -v
+// are first combined into their sum P and difference D, and the moments accumulate c P (even
+// moments) and c D (odd moments) in float.  The odd moments (the velocity) then cancel within each
+// direction pair before they are summed over directions, which keeps T^{0a} near float rounding of
+// the populations (about 1e-8 of T^00; summing +v and -v over all directions first and subtracting
+// at the end loses an order of magnitude more).  Returned in double, with the weights' own moments
+// and T^zz (trace identity) added in double.
 template <class L, bool DEV, class GetF>
-__device__ __forceinline__ Mom<double> moments_ff(GetF&& getf, double c) {
-  const FF z{0.f, 0.f};
-  FF N0 = z, Nx = z, Ny = z, Nz = z, T00 = z, T0x = z, T0y = z, T0z = z, Txx = z, Tyy = z, Txy = z, Txz = z, Tyz = z;
+__device__ __forceinline__ Mom<double> moments_pd(GetF&& getf, double c) {
+  float N0 = 0.f, Nx = 0.f, Ny = 0.f, Nz = 0.f, T00 = 0.f, T0x = 0.f, T0y = 0.f, T0z = 0.f, Txx = 0.f, Tyy = 0.f,
+        Txy = 0.f, Txz = 0.f, Tyz = 0.f;
   static_for<L::NDP>([&](auto K) {
     constexpr int k = decltype(K)::value;
     constexpr int first = L::DP_FIRST[k];
     constexpr int np = L::DP_NPAIR[k];
-    FF S1p = z, S1m = z, S2p = z, S2m = z;
+    float S1p = 0.f, S1m = 0.f, S2p = 0.f, S2m = 0.f;
     static_for<np>([&](auto J) {
       constexpr int ip = first + 2 * decltype(J)::value;
       constexpr double wk = DEV ? L::W[ip] : 1.0;  // mirror partners share the weight
-      constexpr FFC p0 = ffc(wk * L::P0[L::LEV[ip]]);
-      constexpr FFC p02 = ffc(wk * L::P0[L::LEV[ip]] * L::P0[L::LEV[ip]]);
+      constexpr float p0 = (float)(wk * L::P0[L::LEV[ip]]);
+      constexpr float p02 = (float)(wk * L::P0[L::LEV[ip]] * L::P0[L::LEV[ip]]);
       const float fa = getf(ic<ip>{}), fb = getf(ic<ip + 1>{});
-      S1p = ff_add(S1p, ff_mulf(p0, fa));
-      S1m = ff_add(S1m, ff_mulf(p0, fb));
-      S2p = ff_add(S2p, ff_mulf(p02, fa));
-      S2m = ff_add(S2m, ff_mulf(p02, fb));
+      S1p = fmaf(p0, fa, S1p);
+      S1m = fmaf(p0, fb, S1m);
+      S2p = fmaf(p02, fa, S2p);
+      S2m = fmaf(p02, fb, S2m);
     });
     constexpr int vx = L::VX[first], vy = L::VY[first], vz = L::VZ[first];
-    const FF S2 = ff_add(S2p, S2m), D1 = ff_sub(S1p, S1m), D2 = ff_sub(S2p, S2m);
-    N0 = ff_add(N0, ff_add(S1p, S1m));
-    T00 = ff_add(T00, S2);
+    constexpr double ir = L::INV_R, ir2 = L::INV_R2;
+    const float P1 = S1p + S1m, D1 = S1p - S1m, P2 = S2p + S2m, D2 = S2p - S2m;
+    N0 += P1;
+    T00 += P2;
     if constexpr (vx != 0) {
-      Nx = ff_add(Nx, ff_mulc(D1, ffc(vx * L::INV_R)));
-      T0x = ff_add(T0x, ff_mulc(D2, ffc(vx * L::INV_R)));
-      Txx = ff_add(Txx, ff_mulc(S2, ffc(vx * vx * L::INV_R2)));
+      Nx = fmaf((float)(vx * ir), D1, Nx);
+      T0x = fmaf((float)(vx * ir), D2, T0x);
+      Txx = fmaf((float)(vx * vx * ir2), P2, Txx);
     }
     if constexpr (vy != 0) {
-      Ny = ff_add(Ny, ff_mulc(D1, ffc(vy * L::INV_R)));
-      T0y = ff_add(T0y, ff_mulc(D2, ffc(vy * L::INV_R)));
-      Tyy = ff_add(Tyy, ff_mulc(S2, ffc(vy * vy * L::INV_R2)));
+      Ny = fmaf((float)(vy * ir), D1, Ny);
+      T0y = fmaf((float)(vy * ir), D2, T0y);
+      Tyy = fmaf((float)(vy * vy * ir2), P2, Tyy);
     }
     if constexpr (vz != 0) {
-      Nz = ff_add(Nz, ff_mulc(D1, ffc(vz * L::INV_R)));
-      T0z = ff_add(T0z, ff_mulc(D2, ffc(vz * L::INV_R)));
+      Nz = fmaf((float)(vz * ir), D1, Nz);
+      T0z = fmaf((float)(vz * ir), D2, T0z);
     }
-    if constexpr (vx != 0 && vy != 0) Txy = ff_add(Txy, ff_mulc(S2, ffc(vx * vy * L::INV_R2)));
-    if constexpr (vx != 0 && vz != 0) Txz = ff_add(Txz, ff_mulc(S2, ffc(vx * vz * L::INV_R2)));
-    if constexpr (vy != 0 && vz != 0) Tyz = ff_add(Tyz, ff_mulc(S2, ffc(vy * vz * L::INV_R2)));
+    if constexpr (vx != 0 && vy != 0) Txy = fmaf((float)(vx * vy * ir2), P2, Txy);
+    if constexpr (vx != 0 && vz != 0) Txz = fmaf((float)(vx * vz * ir2), P2, Txz);
+    if constexpr (vy != 0 && vz != 0) Tyz = fmaf((float)(vy * vz * ir2), P2, Tyz);
   });
-  Mom<double> m;
-  m.N0 = ff_to_double(N0);
-  m.Nx = ff_to_double(Nx);
-  m.Ny = ff_to_double(Ny);
-  m.Nz = ff_to_double(Nz);
-  m.T00 = ff_to_double(T00);
-  m.T0x = ff_to_double(T0x);
-  m.T0y = ff_to_double(T0y);
-  m.T0z = ff_to_double(T0z);
-  m.Txx = ff_to_double(Txx);
-  m.Tyy = ff_to_double(Tyy);
-  m.Txy = ff_to_double(Txy);
-  m.Txz = ff_to_double(Txz);
-  m.Tyz = ff_to_double(Tyz);
+  Mom<double> m{N0, Nx, Ny, Nz, T00, T0x, T0y, T0z, Txx, Tyy, 0.0, Txy, Txz, Tyz};
   if constexpr (DEV) add_rest_sums<L, double>(m, c);
   m.Tzz = m.T00 - m.Txx - m.Tyy;
   return m;
@@ -1174,19 +1144,28 @@ __global__ void __launch_bounds__(kMomThreads) k_fields(const typename S::T* __r
     m = moments<L, double>([&](auto I) -> double { return src[index(I)]; });
     lw = landau<double, 200>(m);
   } else {
-    // float populations: the per-cell moments in float-float arithmetic (deviations for half
-    // storage), no double operation per population; Landau matching from the float solution
-    // refined in double to 1e-12 U0; the cross-cell sums below in double
+    // float populations: the per-cell moments in float with each direction pair's difference taken
+    // first (moments_pd; deviations for half storage); the cross-cell sums below in double
     constexpr bool DEV = std::is_same<S, StoreF16Dev>::value;
     auto getf = [&](auto I) -> float {
       constexpr int i = decltype(I)::value;
       if constexpr (DEV) return S::template load_dev<L, i>(src + index(I), p);
       else return (float)src[index(I)];
     };
-    m = moments_ff<L, DEV>(getf, (double)p.half_nref);
-    const Landau<float> lf = landau<float, 8>(convert<double, float>(m));
-    if (lf.ok) lw = landau_from<double, 200>(m, (double)lf.U0, (double)lf.Ux, (double)lf.Uy, (double)lf.Uz, 1e-12);
-    else lw = landau<double, 200>(m);
+    m = moments_pd<L, DEV>(getf, (double)p.half_nref);
+    // the step's policy: float solve, double for cells above gamma_thr, for unconverged float
+    // solves, or everywhere with landau_fp64; the result of a float solve is refined by one
+    // double update (n and eps are the double Rayleigh quotients of the float U)
+    const Mom<float> mf = convert<double, float>(m);
+    const float NN = mf.N0 * mf.N0 - mf.Nx * mf.Nx - mf.Ny * mf.Ny - mf.Nz * mf.Nz;
+    bool dbl = p.landau_fp64 || mf.N0 * mf.N0 > p.gamma_thr2 * NN;
+    if (!dbl) {
+      const Landau<float> lf = landau<float, 8>(mf);
+      if (lf.ok && lf.conv)
+        lw = landau_from<double, 1>(m, (double)lf.U0, (double)lf.Ux, (double)lf.Uy, (double)lf.Uz, 1e-10);
+      dbl = !(lf.ok && lf.conv);
+    }
+    if (dbl) lw = landau<double, 200>(m);
   }
   if (valid) {
     const double nan = __longlong_as_double(0x7ff8000000000000ll);

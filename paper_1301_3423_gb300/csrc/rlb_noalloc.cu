@@ -36,7 +36,8 @@ __global__ void __launch_bounds__(kMomThreads) k_densities_noalloc(const typenam
   const bool valid = gid < p.cells;
   const int c = valid ? gid : p.cells - 1;
   // per-cell moments in the arithmetic rlb_moments uses for this storage (double for double
-  // populations; float-float sums for float and half-deviation ones), summed across cells in double
+  // populations; the fields kernel's float sums for float and half-deviation ones), summed across
+  // cells in double
   Mom<double> m;
   if constexpr (std::is_same<typename S::A, double>::value) {
     m = moments<L, double>([&](auto I) -> double { return src[(long long)decltype(I)::value * p.cells + c]; });
@@ -47,7 +48,7 @@ __global__ void __launch_bounds__(kMomThreads) k_densities_noalloc(const typenam
       if constexpr (DEV) return S::template load_dev<L, i>(src + (long long)i * p.cells + c, p);
       else return (float)src[(long long)i * p.cells + c];
     };
-    m = moments_ff<L, DEV>(getf, (double)p.half_nref);
+    m = moments_pd<L, DEV>(getf, (double)p.half_nref);
   }
   double d[5] = {valid ? m.N0 : 0.0, valid ? m.T00 : 0.0, valid ? m.T0x : 0.0, valid ? m.T0y : 0.0,
                  valid ? m.T0z : 0.0};

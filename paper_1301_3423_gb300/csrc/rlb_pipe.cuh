@@ -230,6 +230,7 @@ __device__ __forceinline__ void pipe_body(const PipeParams& pp, const Tiles& til
     const int pw = warp - cons_warps;
     const int P = pp.producers;
     const int mine = (L::Q - pw + P - 1) / P;  // populations of this producer
+    if (tiles.debug() & kDebugStallProducers) return;  // testing: nothing arrives, every wait runs out
     int k = 0;
     bool ok = true;
     for (;; ++k) {
@@ -252,11 +253,22 @@ __device__ __forceinline__ void pipe_body(const PipeParams& pp, const Tiles& til
       const int x0 = seg * TX;
       const bool xperiodic = p.bc[0] == kPeriodic;
       T* const st = stage0 + (size_t)s * kStageElems;
+      // every copy must lie in the buffer and its guard bytes; one that does not is counted and
+      // read from the buffer's start instead (the byte count of the stage stays the same)
+      const long long lo = -(long long)(kPopGuardBytes / sizeof(T));
+      const long long hi = (long long)L::Q * p.cells + kPopGuardBytes / sizeof(T);
+      auto copy = [&](T* d, long long from, int n) {
+        if (from < lo || from + n > hi) {
+          atomicAdd(&tr.status[kStatusBounds], 1);
+          from = 0;
+        }
+        bulk_g2s(d, src + from, (uint32_t)(n * sizeof(T)), &full[s]);
+      };
       for (int i = lane * P + pw; i < L::Q; i += 32 * P) {
         const char4 v = sv[i];
         const int ys = pipe_src_row(y - v.y, p.ny, p.bc[1]);
         const int zs = pipe_src_row(z - v.z, p.nz, p.bc[2]);
-        const T* rowp = src + (long long)i * p.cells + ((long long)zs * p.ny + ys) * p.nx;
+        const long long row0 = (long long)i * p.cells + ((long long)zs * p.ny + ys) * p.nx;
         const int xs = (x0 - v.x) & ~(AL - 1);  // round down to a granule (two's complement: floor)
         T* d = st + i * BX;
         if (xperiodic && (xs < 0 || xs + BX > p.nx)) {
@@ -266,13 +278,13 @@ __device__ __forceinline__ void pipe_body(const PipeParams& pp, const Tiles& til
           while (a < e) {
             const int per = (a >= 0) ? a / p.nx : -((-a + p.nx - 1) / p.nx);
             const int pe = min(e, (per + 1) * p.nx);
-            bulk_g2s(d + (a - xs), rowp + (a - per * p.nx), (uint32_t)((pe - a) * sizeof(T)), &full[s]);
+            copy(d + (a - xs), row0 + (a - per * p.nx), pe - a);
             a = pe;
           }
         } else {
           // x beyond the ends reads neighbouring memory (guard bytes around every buffer); the
           // consumer patches those cells
-          bulk_g2s(d, rowp + xs, (uint32_t)Sh::ROW_BYTES, &full[s]);
+          copy(d, row0 + xs, BX);
         }
       }
     }
@@ -342,7 +354,14 @@ __device__ __forceinline__ void pipe_body(const PipeParams& pp, const Tiles& til
         bool need = false;
         if constexpr (WALLS) need = p.has_wall && beyond_wall<L, i>(cl, p);
         if constexpr (vx != 0) need = need || (!xperiodic && (unsigned)(cl.x - vx) >= (unsigned)p.nx);
-        if (need) lb[i * BX + r] = src[pull_index<L, i, true, WALLS>(cl, p)];
+        if (need) {
+          const long long idx = pull_index<L, i, true, WALLS>(cl, p);
+          if ((unsigned long long)idx < (unsigned long long)((long long)L::Q * p.cells)) {
+            lb[i * BX + r] = src[idx];
+          } else {
+            atomicAdd(&status[kStatusBounds], 1);
+          }
+        }
       });
       fence_proxy_async_smem();
       __syncwarp();
@@ -433,6 +452,7 @@ struct SoloTiles {
   int* status;
   __device__ __forceinline__ TileRef<T> at(long long t) const { return TileRef<T>{p, src, dst, status, (int)t, true}; }
   __device__ __forceinline__ int* timeout_word() const { return status + kStatusTimeout; }
+  __device__ __forceinline__ int debug() const { return p.debug; }
 };
 
 // Many lattices (batch members): tile t belongs to member tile_member[t], whose tiles start at its
@@ -452,6 +472,7 @@ struct BatchTiles {
                       (int)(t - m.pipe_tile_begin), launch < m.steps_left};
   }
   __device__ __forceinline__ int* timeout_word() const { return timeout; }
+  __device__ __forceinline__ int debug() const { return 0; }
 };
 
 // One time step of one lattice.

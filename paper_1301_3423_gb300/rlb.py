@@ -47,6 +47,7 @@ class Params(ctypes.Structure):
         ("n_ref", ctypes.c_double),
         ("step_variant", ctypes.c_int),
         ("stream", ctypes.c_void_p),
+        ("debug_flags", ctypes.c_int),
         ("q", ctypes.c_int),
         ("vel", ctypes.POINTER(ctypes.c_int)),
         ("level", ctypes.POINTER(ctypes.c_int)),
@@ -225,7 +226,7 @@ class RLB:
 
     def __init__(self, shape, order=3, bc=("periodic", "periodic", "periodic"), eta_over_s=0.1, tau_prime=0.0,
                  tau_local_T=True, T_ref=1.0, dx_fm=0.008, T_unit_GeV=0.4, storage="f64", landau_fp64=False,
-                 gamma_thr=2.0, n_ref=1.0, stream=None, quadrature=None, step_variant=-1):
+                 gamma_thr=2.0, n_ref=1.0, stream=None, quadrature=None, step_variant=-1, debug_flags=0):
         self._lib = load()
         nz, ny, nx = shape
         p = Params()
@@ -238,6 +239,7 @@ class RLB:
         p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
         p.landau_fp64, p.gamma_thr, p.n_ref = int(bool(landau_fp64)), gamma_thr, n_ref
         p.step_variant = int(step_variant)
+        p.debug_flags = int(debug_flags)
         if stream is not None:
             p.stream = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
         self._keep = []

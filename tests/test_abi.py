@@ -39,6 +39,7 @@ def test_params_layout_matches_c():
     assert (p.eta_over_s, p.tau_prime, p.tau_local_T, p.T_ref) == (0.1, 0.0, 1, 1.0)
     assert (p.dx_fm, p.T_unit_GeV, p.storage, p.landau_fp64) == (0.008, 0.4, 0, 0)
     assert (p.gamma_thr, p.n_ref, p.step_variant, p.stream, p.q) == (2.0, 1.0, -1, None, 0)
+    assert p.debug_flags == 0
 
 
 @pytest.mark.parametrize("order", [3, 2])

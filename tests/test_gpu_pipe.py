@@ -191,3 +191,26 @@ def test_pipe_equals_register_kernel_with_many_tiles_per_block(storage, pipe, re
     err = pop_err(lat, out[pipe], out[reg], n.max())
     print("%s pipe %d vs register %d: %.2e" % (storage, pipe, reg, err))
     assert err < tol
+
+
+def test_expired_waits_are_reported_and_the_context_stays_usable():
+    """Testing flag: the pipelined step's producers withhold every tile, so each consumer's bounded
+    wait (2 s) runs out; the kernel returns, the next synchronising call reports RLB_ETIMEOUT, and
+    the context keeps working (no GPU fault, no hang)."""
+    shape = (8, 8, 128)
+    n, T, u = gen.smooth_random_fields(shape, seed=3, vmax=0.3, sigma_lnT=0.1)
+    with RLB(shape, order=3, storage="f32", eta_over_s=0.1, step_variant=5, debug_flags=1) as g:
+        assert g.variant == 5
+        g.init(n, T, u)
+        f0 = g.populations()
+        g.step(1)
+        with pytest.raises(rlbmod.RLBError) as e:
+            g.sync()
+        assert e.value.status == rlbmod.RLB_ETIMEOUT
+        g.sync()  # the status was reported once and cleared
+        # the step's result is not a valid state (nothing was written); the context still works and
+        # a state can be restored
+        g.populations()
+        g.set_populations(f0)
+        assert np.array_equal(g.populations(), f0)
+        g.moments()
