@@ -183,9 +183,10 @@ rlb_status rlb_autotune(rlb_ctx* ctx, int reps, int* variant, double ms[RLB_MAX_
  * fill the GPU together.  With a register variant (0..3) every member goes through the register
  * kernels (two launches: the members' interior rows in 32-cell segments, four per tile, then their
  * boundary cells).  With a pipelined variant (4 and up) the members whose rows start on 16-byte
- * boundaries go through one launch of the batched pipelined kernel over their row segments, and
- * the others (e.g. 1 x 1 x N tubes) through the register kernels with the variant a context of
- * that storage runs when it has no pipelined one (3 float, 2 half, 0 double).  Members keep their
+ * boundaries and fill at least 3/4 of the tile lanes go through one launch of the batched
+ * pipelined kernel over their row segments, and the others (e.g. 1 x 1 x N tubes, 32-cell rows in
+ * 128-cell tiles) through the register kernels with the variant a context of that storage runs
+ * when it has no pipelined one (3 float, 2 half, 0 double; see rlb_batch_member_variant).  Members keep their
  * own buffers, parameters, status and step counters; a member's populations after a batched run
  * are bitwise those of the same steps taken alone with the same step-kernel variant.  Members must
  * use the batch's stream.
@@ -223,6 +224,13 @@ rlb_status rlb_batch_autotune(rlb_batch* b, int reps, int* variant, double ms[RL
 /* Force the batch's step variant (numbered as for rlb_autotune; see above for how members are
  * split between kernels).  Errors: RLB_EINVAL for a variant the batch's storage does not have. */
 rlb_status rlb_batch_set_variant(rlb_batch* b, int variant);
+
+/* The step-kernel variant the batch runs the member in `slot` with, under the batch's current
+ * variant: the batch's own, or, for a pipelined variant and a member whose rows do not fill the
+ * tiles (rows not on 16-byte boundaries, or under 3/4 of the tile lanes used), the register
+ * fallback (3 float, 2 half, 0 double).  Running that member alone with this variant gives the
+ * same populations bitwise.  -1 for an empty slot or NULL. */
+int rlb_batch_member_variant(const rlb_batch* b, int slot);
 
 /* Kernel launches the batch has enqueued (-1 for NULL). */
 long rlb_batch_kernel_launches(const rlb_batch* b);

@@ -190,8 +190,16 @@ static int default_variant(const rlb_ctx* c) {
   const int* pref = c->prm.storage == RLB_F32 ? pref_f32 : pref_f16;
   const int n = c->prm.storage == RLB_F32 ? (int)(sizeof(pref_f32) / sizeof(int)) : (int)(sizeof(pref_f16) / sizeof(int));
   if (c->prm.storage != RLB_F64)
-    for (int k = 0; k < n; ++k)
+    for (int k = 0; k < n; ++k) {
+      PipeLayout lay;
+      const bool pipe = pref[k] >= kNumRegVariants;
+      // pipelined shapes only where the rows fill their tiles (pipe_fits); a forced variant may
+      // still run on any lattice whose rows start on 16-byte boundaries
+      if (pipe && (!pipe_layout(pref[k], c->q, (int)c->elem, c->smem_per_sm, c->smem_optin, &lay) ||
+                   !pipe_fits(c->sp.nx, lay.tx, (int)c->elem)))
+        continue;
       if (variant_available(c, pref[k])) return pref[k];
+    }
   return kDefaultStepVariant;
 }
 

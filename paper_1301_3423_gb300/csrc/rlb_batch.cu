@@ -158,7 +158,6 @@ static rlb_status upload_table(rlb_batch* b, long nsteps, int variant, int* nmem
   b->pipe_walls = 0;
   b->pipe_timeout = nullptr;
   const bool pipe = variant >= kNumRegVariants && variant_exists(b, variant, &b->lay);
-  const int A = 16 / elem_of(b->storage);
   for (const Member& m : b->members) {
     if (!m.ctx || m.steps_left <= 0) continue;
     BatchMember d{};
@@ -168,7 +167,7 @@ static rlb_status upload_table(rlb_batch* b, long nsteps, int variant, int* nmem
     d.status = m.ctx->status;
     d.parity0 = m.ctx->cur;
     d.steps_left = (int)std::min<long>(m.steps_left, nsteps);
-    if (pipe && d.p.nx % A == 0) {
+    if (pipe && pipe_fits(d.p.nx, b->lay.tx, elem_of(b->storage))) {
       // pipelined: ceil(nx / TX) tiles per row
       d.pipe_tile_begin = (int)pipe_tm.size();
       const long long nt = (long long)((d.p.nx + b->lay.tx - 1) / b->lay.tx) * d.p.ny * d.p.nz;
@@ -427,6 +426,15 @@ extern "C" rlb_status rlb_batch_set_variant(rlb_batch* b, int variant) {
   if (!variant_exists(b, variant)) return bfail(b, RLB_EINVAL, "rlb_batch_set_variant: no such variant");
   b->variant = variant;
   return RLB_OK;
+}
+
+extern "C" int rlb_batch_member_variant(const rlb_batch* b, int slot) {
+  if (!b || slot < 0 || slot >= (int)b->members.size() || !b->members[slot].ctx) return -1;
+  if (b->variant < kNumRegVariants) return b->variant;
+  PipeLayout lay;
+  if (variant_exists(b, b->variant, &lay) && pipe_fits(b->members[slot].ctx->sp.nx, lay.tx, elem_of(b->storage)))
+    return b->variant;
+  return reg_fallback(b);
 }
 
 extern "C" long rlb_batch_kernel_launches(const rlb_batch* b) { return b ? b->launches : -1; }

@@ -44,6 +44,14 @@ struct PipeLayout {
   int tx, nstage, groups, producers, threads, smem, ctas_per_sm;
 };
 
+// A lattice row of nx cells suits tiles of tx cells when its rows start on 16-byte boundaries and
+// the tiles' lanes are at least 3/4 used (a 32-cell row in 128-cell tiles would leave 3/4 idle).
+inline bool pipe_fits(int nx, int tx, int elem) {
+  if (nx % (16 / elem) != 0) return false;
+  const long long used = (long long)((nx + tx - 1) / tx) * tx;
+  return 4LL * nx >= 3 * used;
+}
+
 inline bool pipe_layout(int v, int q, int elem, int smem_per_sm, int smem_optin, PipeLayout* out) {
   if (v < kNumRegVariants || v >= kNumVariantsTotal) return false;
   const PipeConfig& cf = kPipeConfigs[v - kNumRegVariants];

@@ -62,7 +62,8 @@ DECLARED = ["rlb_default_params", "rlb_bytes_required", "rlb_create", "rlb_init"
             "rlb_sync", "rlb_get_populations", "rlb_set_populations", "rlb_steps_done", "rlb_step_variant", "rlb_kernel_launches",
             "rlb_destroy", "rlb_last_error", "rlb_quadrature", "rlb_autotune", "rlb_totals_noalloc", "rlb_batch_create", "rlb_batch_add",
             "rlb_batch_remove", "rlb_batch_steps_left", "rlb_batch_run", "rlb_batch_autotune",
-            "rlb_batch_set_variant", "rlb_batch_kernel_launches", "rlb_batch_last_error", "rlb_batch_destroy"]
+            "rlb_batch_set_variant", "rlb_batch_member_variant", "rlb_batch_kernel_launches", "rlb_batch_last_error",
+            "rlb_batch_destroy"]
 
 
 def lib_path():
@@ -133,6 +134,8 @@ def load(build_if_missing=True):
     lib.rlb_batch_autotune.restype = ip
     lib.rlb_batch_set_variant.argtypes = [vp, ip]
     lib.rlb_batch_set_variant.restype = ip
+    lib.rlb_batch_member_variant.argtypes = [vp, ip]
+    lib.rlb_batch_member_variant.restype = ip
     lib.rlb_batch_kernel_launches.argtypes = [vp]
     lib.rlb_batch_kernel_launches.restype = ctypes.c_long
     lib.rlb_batch_last_error.argtypes = [vp]
@@ -422,6 +425,10 @@ class Batch:
 
     def set_variant(self, v):
         self._check(self._lib.rlb_batch_set_variant(self._h, int(v)))
+
+    def member_variant(self, slot):
+        """The step variant the batch runs the member in `slot` with (rlb_batch_member_variant)."""
+        return int(self._lib.rlb_batch_member_variant(self._h, int(slot)))
 
     @property
     def kernel_launches(self):

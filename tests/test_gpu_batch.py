@@ -24,6 +24,10 @@ MEMBERS = [
     ((16, 40, 72), (1, 0, 0), 0.1, 17, "random"),
     ((24, 16, 48), (2, 0, 2), 0.1, 13, "random"),
     ((600, 1, 1), (0, 0, 2), 0.1, 19, "tube"),
+    # rows that fill 64- and 128-cell tiles: the batched pipelined kernel's members
+    ((6, 5, 128), (0, 0, 0), 0.1, 9, "random"),
+    ((5, 4, 192), (1, 0, 0), 0.1, 7, "random"),
+    ((4, 6, 128), (2, 0, 2), 0.1, 5, "random"),
 ]
 
 
@@ -50,19 +54,25 @@ def make(order, storage, variant, k, stream=None):
 @pytest.mark.parametrize("graph", [True, False])
 def test_batched_members_equal_solo_runs(order, storage, variant, graph):
     """Variants 0-3: every member on the register kernels.  Variants 4 and up: members whose rows
-    start on 16-byte boundaries on the batched pipelined kernel, the others (1 x 1 x N tubes, a
-    row of 7 cells) on the register kernel the same context would run alone."""
-    solo = []
-    for k in range(len(MEMBERS)):
-        ctx, steps = make(order, storage, variant, k)
-        ctx.step(steps)
-        solo.append(ctx.populations())
-        ctx.close()
+    fill the pipelined tiles (128- and 192-cell rows here) on the batched pipelined kernel, the
+    others (1 x 1 x N tubes, rows of 7 to 72 cells) on the register kernel a context of that
+    storage runs alone; each member equals its solo run with the variant the batch reports."""
     ctxs = [make(order, storage, variant, k) for k in range(len(MEMBERS))]
     with Batch(order, storage) as b:
         if variant >= 0:
             b.set_variant(variant)
         slots = [b.add(c, s) for c, s in ctxs]
+        used = [b.member_variant(s) for s in slots]  # the variant each member runs with in the batch
+        if variant >= 4:
+            assert any(v == variant for v in used) and any(v != variant for v in used)
+        solo = []
+        for k in range(len(MEMBERS)):
+            ctx, steps = make(order, storage, used[k] if variant >= 0 else variant, k)
+            if variant >= 0:
+                assert ctx.variant == used[k]
+            ctx.step(steps)
+            solo.append(ctx.populations())
+            ctx.close()
         active = len(ctxs)
         while active:
             active = b.run(8, graph=graph)  # members stop at their own step counts
