@@ -332,6 +332,13 @@ extern "C" rlb_status rlb_create(const rlb_params* p, rlb_ctx** out) {
 extern "C" rlb_status rlb_destroy(rlb_ctx* c) {
   if (!c) return RLB_OK;
   if (c->stream || c->buf[0]) cudaStreamSynchronize(c->stream);
+  if (c->copy_stream) {
+    cudaStreamSynchronize(c->copy_stream);
+    cudaStreamDestroy(c->copy_stream);
+  }
+  if (c->ev_ready) cudaEventDestroy(c->ev_ready);
+  for (cudaEvent_t& e : c->ev_chunk)
+    if (e) cudaEventDestroy(e);
   for (int b = 0; b < 2; ++b)
     if (c->raw[b]) cudaFree(c->raw[b]);
   if (c->fields) cudaFree(c->fields);
@@ -385,23 +392,57 @@ extern "C" rlb_status rlb_sync(rlb_ctx* c) {
   return read_status(c);
 }
 
+// Chunks of host transfers: ranges of whole kMomThreads-cell blocks, kChunks of them (fewer for
+// small lattices), so that chunk j's copy overlaps chunk j - 1's kernel.
+constexpr int kChunks = 8;
+
+static int chunk_blocks(const rlb_ctx* c) {
+  const int blocks = (c->cells + kMomThreads - 1) / kMomThreads;
+  return (blocks + kChunks - 1) / kChunks;
+}
+
+static rlb_status ensure_copy_stream(rlb_ctx* c) {
+  if (c->copy_stream) return RLB_OK;
+  RLB_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+  RLB_CUDA(c, cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming));
+  for (cudaEvent_t& e : c->ev_chunk) RLB_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  return RLB_OK;
+}
+
 extern "C" rlb_status rlb_init(rlb_ctx* c, const double* n, const double* T, const double* u, int on_device) {
   if (!c) return RLB_EINVAL;
   if (!n || !T || !u) return fail(c, RLB_EINVAL, "rlb_init: null field pointer");
-  const size_t cb = (size_t)c->cells * sizeof(double);
-  const double *dn = n, *dT = T, *du = u;
-  if (!on_device) {
-    RLB_CUDA(c, cudaMemcpyAsync(c->fields, n, cb, cudaMemcpyHostToDevice, c->stream));
-    RLB_CUDA(c, cudaMemcpyAsync(c->fields + c->cells, T, cb, cudaMemcpyHostToDevice, c->stream));
-    RLB_CUDA(c, cudaMemcpyAsync(c->fields + 2 * (size_t)c->cells, u, 3 * cb, cudaMemcpyHostToDevice, c->stream));
-    dn = c->fields;
-    dT = c->fields + c->cells;
-    du = c->fields + 2 * (size_t)c->cells;
+  rlb_status st = RLB_OK;
+  if (on_device) {
+    st = check_launch(c, c->launch->init(n, T, u, c->buf[c->cur], c->sp, c->status, 0, c->cells, c->stream),
+                      "init kernel");
+    if (st != RLB_OK) return st;
+  } else {
+    // host fields: chunk j is copied into the staging buffer on the copy stream while the init
+    // kernel of chunk j - 1 runs on the context's stream
+    st = ensure_copy_stream(c);
+    if (st != RLB_OK) return st;
+    RLB_CUDA(c, cudaEventRecord(c->ev_ready, c->stream));  // earlier work on the staging buffer is done
+    RLB_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->ev_ready, 0));
+    const size_t cells = (size_t)c->cells;
+    const int per = chunk_blocks(c) * kMomThreads;
+    for (int j = 0; j < kChunks; ++j) {
+      const int a = std::min(c->cells, j * per), b = std::min(c->cells, (j + 1) * per);
+      if (a >= b) break;
+      const size_t nb = (size_t)(b - a) * sizeof(double);
+      const double* src[5] = {n + a, T + a, u + a, u + cells + a, u + 2 * cells + a};
+      for (int k = 0; k < 5; ++k)
+        RLB_CUDA(c, cudaMemcpyAsync(c->fields + k * cells + a, src[k], nb, cudaMemcpyHostToDevice, c->copy_stream));
+      RLB_CUDA(c, cudaEventRecord(c->ev_chunk[j], c->copy_stream));
+      RLB_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_chunk[j], 0));
+      st = check_launch(c,
+                        c->launch->init(c->fields, c->fields + cells, c->fields + 2 * cells, c->buf[c->cur], c->sp,
+                                        c->status, a, b, c->stream),
+                        "init kernel");
+      if (st != RLB_OK) return st;
+    }
+    RLB_CUDA(c, cudaStreamSynchronize(c->stream));  // host buffers may be reused (every copy preceded a kernel)
   }
-  rlb_status st =
-      check_launch(c, c->launch->init(dn, dT, du, c->buf[c->cur], c->sp, c->status, c->stream), "init kernel");
-  if (st != RLB_OK) return st;
-  if (!on_device) RLB_CUDA(c, cudaStreamSynchronize(c->stream));  // host buffers may be reused
   c->steps = 0;
   c->have_prev = false;
   return RLB_OK;
@@ -461,17 +502,43 @@ extern "C" rlb_status rlb_moments(rlb_ctx* c, double* n, double* eps, double* U,
   if (!c) return RLB_EINVAL;
   const bool pull = c->have_prev;
   const void* src = pull ? c->buf[1 - c->cur] : c->buf[c->cur];
-  rlb_status st = check_launch(
-      c, c->launch->fields(src, c->sp, c->fields, c->partial, c->status, pull, c->stream), "fields kernel");
-  if (st != RLB_OK) return st;
+  const size_t cells = (size_t)c->cells;
+  rlb_status st = RLB_OK;
+  if (on_device || (!n && !eps && !U)) {
+    st = check_launch(c, c->launch->fields(src, c->sp, c->fields, c->partial, c->status, pull, 0, c->fblocks, c->stream),
+                      "fields kernel");
+    if (st != RLB_OK) return st;
+    const size_t cb = cells * sizeof(double);
+    if (n) RLB_CUDA(c, cudaMemcpyAsync(n, c->fields, cb, cudaMemcpyDeviceToDevice, c->stream));
+    if (eps) RLB_CUDA(c, cudaMemcpyAsync(eps, c->fields + cells, cb, cudaMemcpyDeviceToDevice, c->stream));
+    if (U) RLB_CUDA(c, cudaMemcpyAsync(U, c->fields + 2 * cells, 4 * cb, cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    // host outputs: the fields of chunk j are copied out on the copy stream while the fields kernel
+    // of chunk j + 1 runs on the context's stream
+    st = ensure_copy_stream(c);
+    if (st != RLB_OK) return st;
+    const int per_blocks = chunk_blocks(c);
+    for (int j = 0; j < kChunks; ++j) {
+      const int b0 = std::min(c->fblocks, j * per_blocks), b1 = std::min(c->fblocks, (j + 1) * per_blocks);
+      if (b0 >= b1) break;
+      st = check_launch(c, c->launch->fields(src, c->sp, c->fields, c->partial, c->status, pull, b0, b1, c->stream),
+                        "fields kernel");
+      if (st != RLB_OK) return st;
+      RLB_CUDA(c, cudaEventRecord(c->ev_chunk[j], c->stream));
+      RLB_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->ev_chunk[j], 0));
+      const size_t a = (size_t)b0 * kMomThreads, b = std::min(cells, (size_t)b1 * kMomThreads);
+      const size_t nb = (b - a) * sizeof(double);
+      double* dst[6] = {n ? n + a : nullptr, eps ? eps + a : nullptr, U ? U + a : nullptr, U ? U + cells + a : nullptr,
+                        U ? U + 2 * cells + a : nullptr, U ? U + 3 * cells + a : nullptr};
+      for (int k = 0; k < 6; ++k)
+        if (dst[k]) RLB_CUDA(c, cudaMemcpyAsync(dst[k], c->fields + k * cells + a, nb, cudaMemcpyDeviceToHost,
+                                                c->copy_stream));
+    }
+  }
   st = check_launch(c, launch_reduce_partials(c->partial, c->fblocks, c->totals, c->stream), "reduce kernel");
   if (st != RLB_OK) return st;
-  const size_t cb = (size_t)c->cells * sizeof(double);
-  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  if (n) RLB_CUDA(c, cudaMemcpyAsync(n, c->fields, cb, k, c->stream));
-  if (eps) RLB_CUDA(c, cudaMemcpyAsync(eps, c->fields + c->cells, cb, k, c->stream));
-  if (U) RLB_CUDA(c, cudaMemcpyAsync(U, c->fields + 2 * (size_t)c->cells, 4 * cb, k, c->stream));
   if (totals) RLB_CUDA(c, cudaMemcpyAsync(totals, c->totals, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (c->copy_stream) RLB_CUDA(c, cudaStreamSynchronize(c->copy_stream));
   return read_status(c);
 }
 

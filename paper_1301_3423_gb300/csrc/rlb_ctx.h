@@ -30,5 +30,10 @@ struct rlb_ctx {
   const rlb::Launchers* launch = nullptr;
   int variant = 0;            // step-kernel variant (kNumRegVariants register kernels, then pipelined shapes)
   int sms = 0, smem_per_sm = 0, smem_optin = 0;  // device: SMs, shared memory per SM, per block (opt-in)
+  // host transfers of rlb_init / rlb_moments run in chunks on a copy stream that overlaps the
+  // kernels on `stream` (created on first use)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_ready = nullptr;
+  cudaEvent_t ev_chunk[8] = {nullptr};
   std::string err;
 };

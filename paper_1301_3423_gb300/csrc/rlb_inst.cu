@@ -45,22 +45,24 @@ int batch_blocks_per_sm(int variant) {
 }
 
 cudaError_t fields(const void* src, const StepParams& p, double* f, double* partial, int* status, bool pull,
-                   cudaStream_t s) {
-  const int blocks = (p.cells + kMomThreads - 1) / kMomThreads;
+                   int block0, int block1, cudaStream_t s) {
+  const int blocks = block1 - block0;
+  if (blocks <= 0) return cudaSuccess;
   // the modulo wrap only for lattices with a periodic axis shorter than the stencil reach
   if (pull && p.general)
-    k_fields<L, S, true, true><<<blocks, kMomThreads, 0, s>>>((const T*)src, p, f, partial, status);
+    k_fields<L, S, true, true><<<blocks, kMomThreads, 0, s>>>((const T*)src, p, f, partial, status, block0);
   else if (pull)
-    k_fields<L, S, true, false><<<blocks, kMomThreads, 0, s>>>((const T*)src, p, f, partial, status);
+    k_fields<L, S, true, false><<<blocks, kMomThreads, 0, s>>>((const T*)src, p, f, partial, status, block0);
   else
-    k_fields<L, S, false, false><<<blocks, kMomThreads, 0, s>>>((const T*)src, p, f, partial, status);
+    k_fields<L, S, false, false><<<blocks, kMomThreads, 0, s>>>((const T*)src, p, f, partial, status, block0);
   return cudaGetLastError();
 }
 
 cudaError_t init(const double* n, const double* Tf, const double* u, void* dst, const StepParams& p, int* status,
-                 cudaStream_t s) {
-  const int blocks = (p.cells + 127) / 128;
-  k_init<L, S><<<blocks, 128, 0, s>>>(n, Tf, u, (T*)dst, p, status);
+                 int c0, int c1, cudaStream_t s) {
+  if (c1 <= c0) return cudaSuccess;
+  const int blocks = (c1 - c0 + 127) / 128;
+  k_init<L, S><<<blocks, 128, 0, s>>>(n, Tf, u, (T*)dst, p, status, c0, c1);
   return cudaGetLastError();
 }
 

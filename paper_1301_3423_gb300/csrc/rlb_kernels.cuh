@@ -1130,8 +1130,11 @@ __global__ void __launch_bounds__(kMomThreads) k_fields(const typename S::T* __r
                                                         const __grid_constant__ StepParams p,
                                                         double* __restrict__ fields,
                                                         double* __restrict__ partial,
-                                                        int* __restrict__ status) {
-  const int gid = blockIdx.x * kMomThreads + threadIdx.x;
+                                                        int* __restrict__ status, int block0) {
+  // blocks [block0, block0 + gridDim.x) of the lattice's kMomThreads-cell blocks (a launch may cover
+  // a chunk of the lattice; the partial sums land in the same slots either way)
+  const int blk = block0 + blockIdx.x;
+  const int gid = blk * kMomThreads + threadIdx.x;
   const bool valid = gid < p.cells;
   const Cell cl = make_cell(valid ? gid : p.cells - 1, p);
   auto index = [&](auto I) -> long long {
@@ -1199,7 +1202,7 @@ __global__ void __launch_bounds__(kMomThreads) k_fields(const typename S::T* __r
     double s = 0.0;
 #pragma unroll
     for (int w = 0; w < kMomThreads / 32; ++w) s += ws[w][threadIdx.x];
-    partial[(long long)blockIdx.x * 5 + threadIdx.x] = s;
+    partial[(long long)blk * 5 + threadIdx.x] = s;
   }
 }
 
@@ -1210,9 +1213,11 @@ __global__ void __launch_bounds__(kMomThreads) k_fields(const typename S::T* __r
 template <class L, class S>
 __global__ void __launch_bounds__(128) k_init(const double* __restrict__ n, const double* __restrict__ Tf,
                                               const double* __restrict__ u, typename S::T* __restrict__ dst,
-                                              const __grid_constant__ StepParams p, int* __restrict__ status) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= p.cells) return;
+                                              const __grid_constant__ StepParams p, int* __restrict__ status,
+                                              int c0, int c1) {
+  // cells [c0, c1) (a launch may cover a chunk of the lattice)
+  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= c1) return;
   const long long cells = p.cells;
   const double ux = u[c], uy = u[cells + c], uz = u[2 * cells + c];
   const double u2 = ux * ux + uy * uy + uz * uz;

@@ -13,10 +13,12 @@ struct BatchMember;
 struct Launchers {
   cudaError_t (*step)(const void* src, void* dst, const StepParams& p, int* status, bool general, int variant,
                       cudaStream_t s);
+  // fields and partial sums of the lattice's kMomThreads-cell blocks [block0, block1)
   cudaError_t (*fields)(const void* src, const StepParams& p, double* fields, double* partial, int* status, bool pull,
-                        cudaStream_t s);
+                        int block0, int block1, cudaStream_t s);
+  // initial populations of cells [c0, c1)
   cudaError_t (*init)(const double* n, const double* T, const double* u, void* dst, const StepParams& p, int* status,
-                      cudaStream_t s);
+                      int c0, int c1, cudaStream_t s);
   cudaError_t (*convert)(void* pop, double* dbl, int i0, int i1, bool to_f64, const StepParams& p, cudaStream_t s);
   int step_variants;  // number of step-kernel variants the autotuner may choose from
   // one time step of the persistent batched kernels: a launch over the row tiles [0, row_tiles) and

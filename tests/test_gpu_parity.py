@@ -363,3 +363,34 @@ def test_non_finite_populations_are_reported_as_enan():
         g.set_populations(f0)
         g.step(2)
         g.moments()  # clean again
+
+
+@pytest.mark.parametrize("order", [3, 2])
+@pytest.mark.parametrize("T_ref", [1.0, 2.5])
+def test_reference_temperature_relaxation_time_matches_oracle(order, T_ref):
+    """tau_local_T = 0: tau' from the reference temperature T_ref (Sec. III) instead of each
+    cell's Landau temperature, on the shock tube whose local T differs from T_ref; double storage
+    per population at 1e-12 against the oracle after 30 steps."""
+    lat = oracle.read_lattice(order)
+    n, T, u = gen.riemann_tube(96)
+    o = oracle.OracleRLB(lat, 1, 1, 96, bc=(0, 0, 1), eta_over_s=0.1, tau_local_T=0, T_ref=T_ref)
+    o.init(n, T, u)
+    o.step(30)
+    with RLB((96, 1, 1), order=order, bc=(0, 0, 1), eta_over_s=0.1, tau_local_T=False, T_ref=T_ref) as g:
+        g.init(n, T, u)
+        g.step(30)
+        f = g.populations()
+    assert pop_err(lat, f, o.f, 1.0) < 1e-12
+
+
+def test_context_larger_than_the_device_is_enomem():
+    """rlb_create maps a refused cudaMalloc to RLB_ENOMEM (nothing is launched): 1200^3 float cells
+    need 1.8 TB of populations."""
+    with pytest.raises(RLBError) as e:
+        RLB((1200, 1200, 1200), order=3, storage="f32")
+    assert e.value.status == rlbmod.RLB_ENOMEM
+    with RLB((4, 4, 8), order=3, storage="f32") as g:  # the device is still usable
+        n, T, u = gen.smooth_random_fields((4, 4, 8), seed=1, vmax=0.2, sigma_lnT=0.1)
+        g.init(n, T, u)
+        g.step(1)
+        g.sync()
