@@ -163,11 +163,15 @@ rlb_status rlb_set_populations(rlb_ctx* ctx, const double* f, int on_device);
  *         y and z are interior, then the boundary rows); float and half storage only, except 0:
  *         bit 0 = scalar or mirror pairs in paired-FMA float2 arithmetic, bit 1 = 2 or 3 resident
  *         blocks per SM.  Double storage has variant 0, which reads its populations twice.
- *   4..10 the pipelined kernel, one launch per step: a producer warp stages each tile's pulled
+ *   4..11 the pipelined kernel, one launch per step: producer warps stage each tile's pulled
  *         populations in shared memory with bulk copies and consumer warps relax the cells from
- *         there; the variants differ in tile width (32 or 64 cells), consumer warps per block and
- *         blocks per SM.  Every storage; only for lattices whose nx is a multiple of 16 bytes'
- *         worth of populations (4 float, 8 half, 2 double).
+ *         there; a tile is a 64- or 128-cell segment of a row, and the variants differ in tile
+ *         width, consumer warps and producer warps per block.  Every storage; only for lattices
+ *         whose nx is a multiple of 16 bytes' worth of populations (4 float, 8 half, 2 double).
+ *   12..14 the pipelined kernel with row tiles: a tile is 128 / nx whole rows (one bulk copy per
+ *         population and run of consecutive source rows, the periodic x wrapped in shared memory);
+ *         only for lattices with a periodic x of at most 128 cells (and at least the stencil's
+ *         x reach), nx again a multiple of 16 bytes' worth of populations.
  * Each variant repeats one step from the current populations into the spare buffer `reps` times, so
  * the state does not change; this is allowed only before the first step after rlb_init /
  * rlb_set_populations (RLB_ESTATE otherwise).  *variant (may be NULL) receives the choice;
@@ -183,11 +187,14 @@ rlb_status rlb_autotune(rlb_ctx* ctx, int reps, int* variant, double ms[RLB_MAX_
  * fill the GPU together.  With a register variant (0..3) every member goes through the register
  * kernels (two launches: the members' interior rows in 32-cell segments, four per tile, then their
  * boundary cells).  With a pipelined variant (4 and up) the members whose rows start on 16-byte
- * boundaries and fill at least 3/4 of the tile lanes go through one launch of the batched
- * pipelined kernel over their row segments, and the others (e.g. 1 x 1 x N tubes, 32-cell rows in
- * 128-cell tiles) through the register kernels with the variant a context of that storage runs
- * when it has no pipelined one (3 float, 2 half, 0 double; see rlb_batch_member_variant).  Members keep their
- * own buffers, parameters, status and step counters; a member's populations after a batched run
+ * boundaries and fill at least 7/8 of the tile lanes go through one launch of the batched
+ * pipelined kernel over their row segments; with a row-tile variant (12 and up) the members with a
+ * periodic x of at most 128 cells whose row tiles use at least 3/4 of the lanes go through a
+ * launch of the row-tile kernel, and the wider members through the row-segment
+ * kernel of the same block layout; the others (e.g. 1 x 1 x N tubes) run through the register
+ * kernels with the variant a context of that storage runs when it has no pipelined one (3 float,
+ * 2 half, 0 double; see rlb_batch_member_variant).  Members keep their own buffers, parameters,
+ * status and step counters; a member's populations after a batched run
  * are bitwise those of the same steps taken alone with the same step-kernel variant.  Members must
  * use the batch's stream.
  * ------------------------------------------------------------------------------------------- */
@@ -226,10 +233,10 @@ rlb_status rlb_batch_autotune(rlb_batch* b, int reps, int* variant, double ms[RL
 rlb_status rlb_batch_set_variant(rlb_batch* b, int variant);
 
 /* The step-kernel variant the batch runs the member in `slot` with, under the batch's current
- * variant: the batch's own, or, for a pipelined variant and a member whose rows do not fill the
- * tiles (rows not on 16-byte boundaries, or under 3/4 of the tile lanes used), the register
- * fallback (3 float, 2 half, 0 double).  Running that member alone with this variant gives the
- * same populations bitwise.  -1 for an empty slot or NULL. */
+ * variant: the batch's own; for a row-tile variant and a member that runs in row segments, the
+ * row-segment variant of the same block layout; for a pipelined variant and a member whose rows do
+ * not suit the tiles, the register fallback (3 float, 2 half, 0 double).  Running that member
+ * alone with this variant gives the same populations bitwise.  -1 for an empty slot or NULL. */
 int rlb_batch_member_variant(const rlb_batch* b, int slot);
 
 /* Kernel launches the batch has enqueued (-1 for NULL). */

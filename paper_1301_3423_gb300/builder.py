@@ -24,8 +24,8 @@ NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-
 INSTANCES = [(o, s) for o in (3, 2) for s in (0, 1, 2)]
 # step-kernel variants compiled per (order, storage): one for double storage, four for float ones
 VARIANT_UNITS = [(o, s, v) for o, s in INSTANCES for v in ((0,) if s == 0 else (0, 1, 2, 3))]
-# pipelined step kernel per (order, storage) and tile width
-PIPE_UNITS = [(o, s, tx) for o, s in INSTANCES for tx in (64, 128)]
+# pipelined step kernel per (order, storage), tile width and tile kind (row tiles: width 128 only)
+PIPE_UNITS = [(o, s, tx, rows) for o, s in INSTANCES for tx, rows in ((64, 0), (128, 0), (128, 1))]
 
 
 def _nvcc():
@@ -86,10 +86,10 @@ def build(force=False, verbose=False):
         jobs.append((obj, [nvcc] + NVCC_FLAGS + inc + ["-DRLB_INST_ORDER=%d" % o, "-DRLB_INST_STORAGE=%d" % s,
                                                           "-DRLB_INST_VARIANT=%d" % v, "-c",
                                                           os.path.join(CSRC, "rlb_inst_variant.cu"), "-o", obj]))
-    for o, s, tx in PIPE_UNITS:
-        obj = os.path.join(BUILD, "rlb_inst_o%d_s%d_x%d.o" % (o, s, tx))
+    for o, s, tx, rows in PIPE_UNITS:
+        obj = os.path.join(BUILD, "rlb_inst_o%d_s%d_%s%d.o" % (o, s, "r" if rows else "x", tx))
         jobs.append((obj, [nvcc] + NVCC_FLAGS + inc + ["-DRLB_INST_ORDER=%d" % o, "-DRLB_INST_STORAGE=%d" % s,
-                                                          "-DRLB_INST_TX=%d" % tx, "-c",
+                                                          "-DRLB_INST_TX=%d" % tx, "-DRLB_INST_ROWS=%d" % rows, "-c",
                                                           os.path.join(CSRC, "rlb_inst_pipe.cu"), "-o", obj]))
     # longest units first so the parallel build ends sooner
     jobs = jobs[:1] + sorted(jobs[1:], key=lambda j: ("_v" not in j[0], "_s0" in j[0]))

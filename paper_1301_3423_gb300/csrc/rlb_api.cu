@@ -157,20 +157,25 @@ static bool needs_general_wrap(const rlb_params& p) {
          (p.bc[2] == RLB_BC_PERIODIC && p.nz < L::VMAX_Z);
 }
 
+static int vmax_x(const rlb_ctx* c) { return c->prm.order == 3 ? Quad3::VMAX_X : Quad2::VMAX_X; }
+
 // Shape of pipelined variant v (>= kNumRegVariants) on this context's lattice: the block layout
 // (pipe_layout) and the tiles.  False if the variant does not exist or the lattice cannot use it
-// (rows must start on 16-byte boundaries).
-static bool pipe_shape(const rlb_ctx* c, int v, PipeParams* pp, int* grid, int* threads, int* smem, int* tx = nullptr) {
+// (rows must start on 16-byte boundaries; row tiles also need a periodic x of vmax_x .. tx cells).
+static bool pipe_shape(const rlb_ctx* c, int v, PipeParams* pp, int* grid, int* threads, int* smem, int* tx = nullptr,
+                       int* rows = nullptr) {
   PipeLayout lay;
   if (c->sms <= 0 || !pipe_layout(v, c->q, (int)c->elem, c->smem_per_sm, c->smem_optin, &lay)) return false;
   if (c->sp.nx % (16 / (int)c->elem) != 0) return false;
-  const long long ntiles = (long long)((c->sp.nx + lay.tx - 1) / lay.tx) * c->sp.ny * c->sp.nz;
+  if (lay.rows && !rows_possible(c->sp.nx, lay.tx, (int)c->elem, c->sp.bc[0], vmax_x(c))) return false;
+  const long long ntiles = pipe_tile_count(c->sp.nx, c->sp.ny, c->sp.nz, lay.tx, lay.rows);
   if (ntiles > 0x7fffffffll) return false;
   if (pp) *pp = PipeParams{lay.producers, (int)ntiles, lay.nstage, lay.groups};
   if (grid) *grid = (int)std::min<long long>((long long)c->sms * lay.ctas_per_sm, ntiles);
   if (threads) *threads = lay.threads;
   if (smem) *smem = lay.smem;
   if (tx) *tx = lay.tx;
+  if (rows) *rows = lay.rows;
   return true;
 }
 
@@ -180,23 +185,25 @@ static bool variant_available(const rlb_ctx* c, int v) {
   return pipe_shape(c, v, nullptr, nullptr, nullptr, nullptr);
 }
 
-// The variant rlb_step uses unless asked otherwise: the first one that exists for the context in
-// an order measured on GB300 (256^3 and 128^3 lattices, third order): the pipelined shapes for
-// float and half storage, the register kernel for double storage (whose step is bound by the
-// double-precision pipe, which the register kernel's 4 warps per scheduler keep busier).
+// The variant rlb_step uses unless asked otherwise: the first one that suits the context in an
+// order measured on GB300 (32^3 to 256^3 lattices, third order): row segments, then row tiles for
+// float storage, row tiles first for half storage (whose 128-cell rows step 1.26x faster in row
+// tiles), then the register kernels; the register kernel for double storage (whose step is bound
+// by the double-precision pipe, which the register kernel's 4 warps per scheduler keep busier).
 static int default_variant(const rlb_ctx* c) {
-  static const int pref_f32[] = {5, 4, 8, 6, 9, 7, 3};
-  static const int pref_f16[] = {4, 8, 6, 5, 9, 7, 2};
+  static const int pref_f32[] = {5, 12, 4, 13, 8, 6, 9, 7, 3};
+  static const int pref_f16[] = {12, 13, 4, 8, 6, 5, 9, 7, 2};
   const int* pref = c->prm.storage == RLB_F32 ? pref_f32 : pref_f16;
   const int n = c->prm.storage == RLB_F32 ? (int)(sizeof(pref_f32) / sizeof(int)) : (int)(sizeof(pref_f16) / sizeof(int));
   if (c->prm.storage != RLB_F64)
     for (int k = 0; k < n; ++k) {
       PipeLayout lay;
       const bool pipe = pref[k] >= kNumRegVariants;
-      // pipelined shapes only where the rows fill their tiles (pipe_fits); a forced variant may
-      // still run on any lattice whose rows start on 16-byte boundaries
-      if (pipe && (!pipe_layout(pref[k], c->q, (int)c->elem, c->smem_per_sm, c->smem_optin, &lay) ||
-                   !pipe_fits(c->sp.nx, lay.tx, (int)c->elem)))
+      // pipelined shapes only where the lattice's rows fill their tiles (rows_fit_solo for row
+      // tiles, pipe_fits for row segments); a forced variant may still run on any lattice it can take
+      if (pipe && !pipe_layout(pref[k], c->q, (int)c->elem, c->smem_per_sm, c->smem_optin, &lay)) continue;
+      if (pipe && (lay.rows ? !rows_fit_solo(c->sp.nx, lay.tx, (int)c->elem, c->sp.bc[0], vmax_x(c))
+                            : !pipe_fits(c->sp.nx, lay.tx, (int)c->elem)))
         continue;
       if (variant_available(c, pref[k])) return pref[k];
     }
@@ -210,11 +217,12 @@ static rlb_status check_launch(rlb_ctx* c, cudaError_t e, const char* what);
 static rlb_status launch_step(rlb_ctx* c, int v) {
   if (v >= kNumRegVariants) {
     PipeParams pp;
-    int grid = 0, threads = 0, smem = 0, tx = 0;
-    if (!pipe_shape(c, v, &pp, &grid, &threads, &smem, &tx)) return fail(c, RLB_EINVAL, "step variant not available");
+    int grid = 0, threads = 0, smem = 0, tx = 0, rows = 0;
+    if (!pipe_shape(c, v, &pp, &grid, &threads, &smem, &tx, &rows))
+      return fail(c, RLB_EINVAL, "step variant not available");
     return check_launch(c,
-                        c->launch->pipe_step(c->buf[c->cur], c->buf[1 - c->cur], c->sp, pp, c->status, tx, grid,
-                                             threads, smem, c->stream),
+                        c->launch->pipe_step(c->buf[c->cur], c->buf[1 - c->cur], c->sp, pp, c->status, tx, rows,
+                                             grid, threads, smem, c->stream),
                         "pipelined step kernel");
   }
   rlb_status st = check_launch(

@@ -12,6 +12,7 @@
 #include "rlb_common.h"
 #include "rlb_ctx.h"
 #include "rlb_launch.h"
+#include "rlb_quadrature.h"
 
 using namespace rlb;
 
@@ -25,7 +26,8 @@ struct Member {
 struct GraphCache {
   cudaGraphExec_t exec = nullptr;
   long nsteps = 0, version = -1;
-  int variant = -1, nmembers = 0, tiles = 0, row_tiles = -1, walls = -1, pipe_tiles = -1, pipe_walls = -1;
+  int variant = -1, nmembers = 0, tiles = 0, row_tiles = -1, walls = -1, pipe_tiles = -1, pipe_walls = -1,
+      rtile_tiles = -1;
 };
 
 }  // namespace
@@ -42,13 +44,17 @@ struct rlb_batch {
   long counters_capacity = 0;
   const Launchers* launch = nullptr;
   int variant = 0;               // step variant: 0..3 register kernels for every member; 4 and up the
-                                 // pipelined kernel for members whose rows start on 16-byte boundaries
-                                 // and the register fallback (reg_fallback) for the others
+                                 // pipelined kernel for the members whose rows suit it (row tiles for
+                                 // rows_fit members if the variant has row tiles, row segments for
+                                 // pipe_fits members) and the register fallback (reg_fallback) for the others
   int walls = 0;                 // some register-kernel member of the uploaded table has bounce-back walls
   int row_tiles = 0, shell_tiles = 0;  // of the uploaded table: row tiles first, then shell tiles
   int* d_pipe_tm = nullptr;      // member index of every pipelined tile of the uploaded table
   int pipe_tm_capacity = 0;
   int pipe_tiles = 0, pipe_walls = 0;
+  int* d_rtile_tm = nullptr;     // member index of every row tile (pipelined kernel with row tiles)
+  int rtile_tm_capacity = 0;
+  int rtile_tiles = 0;
   int* pipe_timeout = nullptr;   // status word that counts the pipelined kernel's expired waits
   PipeLayout lay{};              // block layout of the current pipelined variant
   int sms = 0, smem_per_sm = 0, smem_optin = 0;
@@ -111,6 +117,49 @@ static bool variant_exists(const rlb_batch* b, int v, PipeLayout* lay = nullptr)
   return pipe_layout(v, q, elem_of(b->storage), b->smem_per_sm, b->smem_optin, lay);
 }
 
+// How a member runs under step variant v: 2 row tiles, 1 row segments (pipelined kernel), 0 the
+// register kernels (variant v itself, or reg_fallback for a pipelined v).
+static int member_mode(const rlb_batch* b, const StepParams& p, int v, const PipeLayout& lay) {
+  if (v < kNumRegVariants) return 0;
+  const int vmax = b->order == 3 ? Quad3::VMAX_X : Quad2::VMAX_X;
+  if (lay.rows && rows_fit(p.nx, lay.tx, elem_of(b->storage), p.bc[0], vmax)) return 2;
+  return pipe_fits(p.nx, lay.tx, elem_of(b->storage)) ? 1 : 0;
+}
+
+// The row-segment variant with the block layout of row-tile variant v (the shape the batch runs its
+// row-segment members in); v itself if it has no row tiles, -1 if none exists.
+static int segment_sibling(int v) {
+  if (v < kNumRegVariants || v >= kNumVariantsTotal) return v;
+  const PipeConfig& c = kPipeConfigs[v - kNumRegVariants];
+  if (!c.rows) return v;
+  for (int k = 0; k < kNumPipeConfigs; ++k) {
+    const PipeConfig& d = kPipeConfigs[k];
+    if (!d.rows && d.tx == c.tx && d.cons_warps == c.cons_warps && d.ctas_per_sm == c.ctas_per_sm &&
+        d.producers == c.producers)
+      return kNumRegVariants + k;
+  }
+  return -1;
+}
+
+// Grow a device tile table to hold n entries and upload `tm` into it.
+static rlb_status upload_tiles(rlb_batch* b, int** d, int* capacity, const std::vector<int>& tm, const char* what) {
+  if ((int)tm.size() > *capacity) {
+    if (*d) cudaFree(*d);
+    *d = nullptr;
+    const int cap = std::max<int>((int)tm.size(), 2 * *capacity);
+    cudaError_t e = cudaMalloc((void**)d, (size_t)cap * sizeof(int));
+    if (e != cudaSuccess) {
+      *capacity = 0;
+      return bfail(b, RLB_ENOMEM, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+    *capacity = cap;
+    ++b->version;  // a captured graph holds the old table pointer
+  }
+  if (!tm.empty())
+    BATCH_CUDA(b, cudaMemcpyAsync(*d, tm.data(), tm.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+  return RLB_OK;
+}
+
 extern "C" rlb_status rlb_batch_add(rlb_batch* b, rlb_ctx* ctx, long steps, int* slot) {
   if (!b) return RLB_EINVAL;
   if (!ctx || steps < 0) return bfail(b, RLB_EINVAL, "rlb_batch_add: null context or negative steps");
@@ -153,11 +202,12 @@ extern "C" long rlb_batch_steps_left(const rlb_batch* b, int slot) {
 // shell tiles for the others).
 static rlb_status upload_table(rlb_batch* b, long nsteps, int variant, int* nmembers, int* total_tiles) {
   std::vector<BatchMember> t;
-  std::vector<int> row_tm, shell_tm, pipe_tm;
+  std::vector<int> row_tm, shell_tm, pipe_tm, rtile_tm;
   b->walls = 0;
   b->pipe_walls = 0;
   b->pipe_timeout = nullptr;
   const bool pipe = variant >= kNumRegVariants && variant_exists(b, variant, &b->lay);
+  if (!pipe) b->lay = PipeLayout{};
   for (const Member& m : b->members) {
     if (!m.ctx || m.steps_left <= 0) continue;
     BatchMember d{};
@@ -167,12 +217,14 @@ static rlb_status upload_table(rlb_batch* b, long nsteps, int variant, int* nmem
     d.status = m.ctx->status;
     d.parity0 = m.ctx->cur;
     d.steps_left = (int)std::min<long>(m.steps_left, nsteps);
-    if (pipe && pipe_fits(d.p.nx, b->lay.tx, elem_of(b->storage))) {
-      // pipelined: ceil(nx / TX) tiles per row
-      d.pipe_tile_begin = (int)pipe_tm.size();
-      const long long nt = (long long)((d.p.nx + b->lay.tx - 1) / b->lay.tx) * d.p.ny * d.p.nz;
-      if ((long long)pipe_tm.size() + nt > 0x7fffffffll) return bfail(b, RLB_EINVAL, "too many tiles in one batch");
-      pipe_tm.resize(pipe_tm.size() + nt, (int)t.size());
+    const int mode = member_mode(b, d.p, pipe ? variant : 0, b->lay);
+    if (mode > 0) {
+      // pipelined: ceil(nx / TX) segment tiles per row, or groups of TX / nx rows
+      std::vector<int>& tm = mode == 2 ? rtile_tm : pipe_tm;
+      d.pipe_tile_begin = (int)tm.size();
+      const long long nt = pipe_tile_count(d.p.nx, d.p.ny, d.p.nz, b->lay.tx, mode == 2);
+      if ((long long)tm.size() + nt > 0x7fffffffll) return bfail(b, RLB_EINVAL, "too many tiles in one batch");
+      tm.resize(tm.size() + nt, (int)t.size());
       if (d.p.has_wall) b->pipe_walls = 1;
       if (!b->pipe_timeout) b->pipe_timeout = d.status + kStatusTimeout;
       t.push_back(d);
@@ -192,28 +244,18 @@ static rlb_status upload_table(rlb_batch* b, long nsteps, int variant, int* nmem
   b->row_tiles = (int)row_tm.size();
   b->shell_tiles = (int)shell_tm.size();
   b->pipe_tiles = (int)pipe_tm.size();
+  b->rtile_tiles = (int)rtile_tm.size();
   for (BatchMember& d : t) d.shell_tile_begin += b->row_tiles;
   std::vector<int> tm(row_tm);
   tm.insert(tm.end(), shell_tm.begin(), shell_tm.end());
   const int tiles = (int)tm.size();
   *nmembers = (int)t.size();
-  *total_tiles = tiles + b->pipe_tiles;
+  *total_tiles = tiles + b->pipe_tiles + b->rtile_tiles;
   if (t.empty()) return RLB_OK;
-  if (b->pipe_tiles > b->pipe_tm_capacity) {
-    if (b->d_pipe_tm) cudaFree(b->d_pipe_tm);
-    b->d_pipe_tm = nullptr;
-    const int cap = std::max<int>(b->pipe_tiles, 2 * b->pipe_tm_capacity);
-    cudaError_t e = cudaMalloc((void**)&b->d_pipe_tm, (size_t)cap * sizeof(int));
-    if (e != cudaSuccess) {
-      b->pipe_tm_capacity = 0;
-      return bfail(b, RLB_ENOMEM, std::string("pipelined tile table: ") + cudaGetErrorString(e));
-    }
-    b->pipe_tm_capacity = cap;
-    ++b->version;  // a captured graph holds the old table pointer
-  }
-  if (b->pipe_tiles > 0)
-    BATCH_CUDA(b, cudaMemcpyAsync(b->d_pipe_tm, pipe_tm.data(), pipe_tm.size() * sizeof(int), cudaMemcpyHostToDevice,
-                                  b->stream));
+  rlb_status st = upload_tiles(b, &b->d_pipe_tm, &b->pipe_tm_capacity, pipe_tm, "pipelined tile table");
+  if (st != RLB_OK) return st;
+  st = upload_tiles(b, &b->d_rtile_tm, &b->rtile_tm_capacity, rtile_tm, "row-tile table");
+  if (st != RLB_OK) return st;
   if ((int)t.size() > b->d_capacity) {
     if (b->d_members) cudaFree(b->d_members);
     b->d_members = nullptr;
@@ -267,11 +309,13 @@ static int grid_of(rlb_batch* b, int variant) { return b->sms * b->launch->batch
 // the register kernels (row tiles, shell tiles) over the other members' tiles.
 static rlb_status enqueue_step(rlb_batch* b, int k, int variant, int* counters) {
   cudaError_t e = cudaSuccess;
-  if (b->pipe_tiles > 0) {
-    const PipeParams pp{b->lay.producers, b->pipe_tiles, b->lay.nstage, b->lay.groups};
-    const int grid = std::min(b->sms * b->lay.ctas_per_sm, b->pipe_tiles);
-    e = b->launch->pipe_batch_step(b->d_members, b->d_pipe_tm, k, pp, b->pipe_timeout, b->lay.tx, b->pipe_walls, grid,
-                                   b->lay.threads, b->lay.smem, b->stream);
+  for (int rows = 0; rows < 2; ++rows) {
+    const int ntiles = rows ? b->rtile_tiles : b->pipe_tiles;
+    if (ntiles == 0) continue;
+    const PipeParams pp{b->lay.producers, ntiles, b->lay.nstage, b->lay.groups};
+    const int grid = std::min(b->sms * b->lay.ctas_per_sm, ntiles);
+    e = b->launch->pipe_batch_step(b->d_members, rows ? b->d_rtile_tm : b->d_pipe_tm, k, pp, b->pipe_timeout,
+                                   b->lay.tx, rows, b->pipe_walls, grid, b->lay.threads, b->lay.smem, b->stream);
     ++b->launches;
     if (e != cudaSuccess) return bfail(b, RLB_ECUDA, std::string("batched pipelined step: ") + cudaGetErrorString(e));
   }
@@ -318,7 +362,7 @@ extern "C" rlb_status rlb_batch_run(rlb_batch* b, long nsteps, int use_graph, in
       GraphCache& gc = b->graph;
       if (!gc.exec || gc.nsteps != nsteps || gc.version != b->version || gc.variant != b->variant ||
           gc.nmembers != nmem || gc.tiles != tiles || gc.row_tiles != b->row_tiles || gc.walls != b->walls ||
-          gc.pipe_tiles != b->pipe_tiles || gc.pipe_walls != b->pipe_walls) {
+          gc.pipe_tiles != b->pipe_tiles || gc.pipe_walls != b->pipe_walls || gc.rtile_tiles != b->rtile_tiles) {
         if (b->graph.exec) cudaGraphExecDestroy(b->graph.exec);
         b->graph.exec = nullptr;
         cudaStream_t cs;
@@ -350,9 +394,10 @@ extern "C" rlb_status rlb_batch_run(rlb_batch* b, long nsteps, int use_graph, in
         gc.walls = b->walls;
         gc.pipe_tiles = b->pipe_tiles;
         gc.pipe_walls = b->pipe_walls;
+        gc.rtile_tiles = b->rtile_tiles;
       }
       BATCH_CUDA(b, cudaGraphLaunch(b->graph.exec, b->stream));
-      b->launches += nsteps * ((b->row_tiles > 0) + (b->shell_tiles > 0) + (b->pipe_tiles > 0));
+      b->launches += nsteps * ((b->row_tiles > 0) + (b->shell_tiles > 0) + (b->pipe_tiles > 0) + (b->rtile_tiles > 0));
     } else {
       rlb_status st = enqueue_run(b, nsteps, nmem, tiles, b->variant);
       if (st != RLB_OK) return st;
@@ -432,8 +477,10 @@ extern "C" int rlb_batch_member_variant(const rlb_batch* b, int slot) {
   if (!b || slot < 0 || slot >= (int)b->members.size() || !b->members[slot].ctx) return -1;
   if (b->variant < kNumRegVariants) return b->variant;
   PipeLayout lay;
-  if (variant_exists(b, b->variant, &lay) && pipe_fits(b->members[slot].ctx->sp.nx, lay.tx, elem_of(b->storage)))
-    return b->variant;
+  if (!variant_exists(b, b->variant, &lay)) return reg_fallback(b);
+  const int mode = member_mode(b, b->members[slot].ctx->sp, b->variant, lay);
+  if (mode == 2) return b->variant;
+  if (mode == 1) return segment_sibling(b->variant);
   return reg_fallback(b);
 }
 
@@ -448,6 +495,7 @@ extern "C" rlb_status rlb_batch_destroy(rlb_batch* b) {
   if (b->d_members) cudaFree(b->d_members);
   if (b->d_tile_member) cudaFree(b->d_tile_member);
   if (b->d_pipe_tm) cudaFree(b->d_pipe_tm);
+  if (b->d_rtile_tm) cudaFree(b->d_rtile_tm);
   if (b->d_counters) cudaFree(b->d_counters);
   delete b;
   return RLB_OK;

@@ -19,12 +19,15 @@ struct PipeConfig {
                     // (two warps per cell); a multiple of the warps per tile
   int ctas_per_sm;  // resident blocks per SM (the shared memory is split between them)
   int producers;    // producer warps per block (each copies every producers-th population of every tile)
+  int rows;         // 0: a tile is a TX-cell segment of one row; 1: a tile is TX / nx whole rows of
+                    // an x-periodic lattice with nx <= TX ("row tiles", one copy per population)
 };
 // A block's stage count is a multiple of its consumer-group count, so that every stage is read by
 // one consumer group, in the order of the stage's uses like every producer: a parity wait then
 // always refers to the phase it means.
-constexpr PipeConfig kPipeConfigs[] = {{128, 8, 1, 8}, {128, 8, 1, 4}, {64, 8, 1, 8}, {64, 4, 1, 4},
-                                       {128, 8, 1, 6}, {64, 8, 1, 4}, {128, 4, 1, 4}, {64, 2, 1, 4}};
+constexpr PipeConfig kPipeConfigs[] = {{128, 8, 1, 8, 0}, {128, 8, 1, 4, 0}, {64, 8, 1, 8, 0}, {64, 4, 1, 4, 0},
+                                       {128, 8, 1, 6, 0}, {64, 8, 1, 4, 0}, {128, 4, 1, 4, 0}, {64, 2, 1, 4, 0},
+                                       {128, 8, 1, 4, 1}, {128, 8, 1, 8, 1}, {128, 4, 1, 4, 1}};
 constexpr int kNumPipeConfigs = sizeof(kPipeConfigs) / sizeof(kPipeConfigs[0]);
 constexpr int kNumVariantsTotal = kNumRegVariants + kNumPipeConfigs;
 constexpr int kPipeMaxStages = 16;
@@ -88,10 +91,11 @@ enum : int {
 enum : int { kDebugStallProducers = 1 };  // the pipelined step's producers do nothing: every wait runs out
 
 // Launch shape of a pipelined step (k_step_pipe, k_step_pipe_batch): tiles are TX-cell segments of
-// the lattice rows, tile t = row * ceil(nx / TX) + seg; block b takes tiles b, b + grid, ...
+// the lattice rows, tile t = row * ceil(nx / TX) + seg, or with row tiles groups of TX / nx
+// consecutive rows, tile t = rows t G .. t G + G - 1; block b takes tiles b, b + grid, ...
 struct PipeParams {
   int producers;  // producer warps per block
-  int ntiles;     // tiles of the launch: ceil(nx / TX) * ny * nz per lattice
+  int ntiles;     // tiles of the launch: ceil(nx / TX) * ny * nz per lattice (ceil(ny nz / G) with row tiles)
   int nstage;     // shared-memory stages per block (<= 16)
   int groups;     // consumer groups per block (TX / 32 warps each, twice that for float storage)
 };

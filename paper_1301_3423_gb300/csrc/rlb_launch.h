@@ -29,13 +29,15 @@ struct Launchers {
                             int launch_index, int* counters, int variant, int walls, int grid, cudaStream_t s);
   // resident blocks per SM of the batched step for a variant
   int (*batch_blocks_per_sm)(int variant);
-  // one time step of the pipelined kernel with tile width tx (64 or 128)
+  // one time step of the pipelined kernel with tile width tx (64 or 128), row tiles if rows != 0
+  // (tx 128 only)
   cudaError_t (*pipe_step)(const void* src, void* dst, const StepParams& p, const PipeParams& pp, int* status, int tx,
-                           int grid, int threads, int smem, cudaStream_t s);
+                           int rows, int grid, int threads, int smem, cudaStream_t s);
   // one time step of the batched pipelined kernel (launch index `launch`) over the members' tiles;
   // walls != 0 selects the kernel with the bounce-back patch
   cudaError_t (*pipe_batch_step)(const BatchMember* members, const int* tile_member, int launch, const PipeParams& pp,
-                                 int* timeout, int tx, int walls, int grid, int threads, int smem, cudaStream_t s);
+                                 int* timeout, int tx, int rows, int walls, int grid, int threads, int smem,
+                                 cudaStream_t s);
 };
 
 // Block layout of pipelined variant v (>= kNumRegVariants) for q populations of `elem` bytes:
@@ -43,15 +45,47 @@ struct Launchers {
 // block, at least two per group), groups, threads and shared-memory bytes.  False if the variant
 // does not exist for this storage.
 struct PipeLayout {
-  int tx, nstage, groups, producers, threads, smem, ctas_per_sm;
+  int tx, nstage, groups, producers, threads, smem, ctas_per_sm, rows;
 };
 
 // A lattice row of nx cells suits tiles of tx cells when its rows start on 16-byte boundaries and
-// the tiles' lanes are at least 3/4 used (a 32-cell row in 128-cell tiles would leave 3/4 idle).
+// the tiles' lanes are at least 7/8 used (a 96-cell row in 128-cell tiles leaves 1/4 idle and ran
+// slower than the register kernel).
 inline bool pipe_fits(int nx, int tx, int elem) {
   if (nx % (16 / elem) != 0) return false;
   const long long used = (long long)((nx + tx - 1) / tx) * tx;
-  return 4LL * nx >= 3 * used;
+  return 8LL * nx >= 7 * used;
+}
+
+// Row tiles of tx cells can take a lattice whose x axis is periodic and at least the stencil reach
+// vmax_x long (one wrap per pull), with nx <= tx cells per row starting on 16-byte boundaries.
+inline bool rows_possible(int nx, int tx, int elem, int bc_x, int vmax_x) {
+  return bc_x == kPeriodic && nx <= tx && nx >= vmax_x && nx % (16 / elem) == 0;
+}
+
+// ... and suit it when the tile's G = tx / nx rows use at least 3/4 of its lanes (the batch's
+// rule: in the batched mix of 32- to 128-cell rows every such member stepped faster in row tiles
+// than on the register kernels).
+inline bool rows_fit(int nx, int tx, int elem, int bc_x, int vmax_x) {
+  return rows_possible(nx, tx, elem, bc_x, vmax_x) && 4 * (tx / nx) * nx >= 3 * tx;
+}
+
+// A single lattice's rule: several rows per tile (G >= 2) at 3/4 of the lanes, or one row that
+// fills the tile (measured on GB300 alone: 32-, 48- and 64-cell rows as fast as or faster than the
+// register kernels, 128-cell rows as fast as row segments with float storage and 1.26x faster with
+// half storage, while one 96-cell row per tile ran 1.4x slower than the register kernels).
+inline bool rows_fit_solo(int nx, int tx, int elem, int bc_x, int vmax_x) {
+  if (!rows_fit(nx, tx, elem, bc_x, vmax_x)) return false;
+  return tx / nx >= 2 || nx == tx;
+}
+
+// Tiles of one lattice: row tiles (groups of tx / nx rows) or tx-cell row segments.
+inline long long pipe_tile_count(int nx, int ny, int nz, int tx, int rows) {
+  if (rows) {
+    const long long g = tx / nx;
+    return ((long long)ny * nz + g - 1) / g;
+  }
+  return (long long)((nx + tx - 1) / tx) * ny * nz;
 }
 
 inline bool pipe_layout(int v, int q, int elem, int smem_per_sm, int smem_optin, PipeLayout* out) {
@@ -74,7 +108,7 @@ inline bool pipe_layout(int v, int q, int elem, int smem_per_sm, int smem_optin,
   const int nstage = (int)(fit / groups * groups);
   if (nstage < 2 * groups) return false;
   if (out) *out = PipeLayout{cf.tx, nstage, groups, cf.producers, (cf.cons_warps + cf.producers) * 32,
-                             (int)(kPipeHeaderBytes + nstage * stage + xchg), cf.ctas_per_sm};
+                             (int)(kPipeHeaderBytes + nstage * stage + xchg), cf.ctas_per_sm, cf.rows};
   return true;
 }
 

@@ -19,6 +19,13 @@
 // so a consumer needs ~100 registers instead of Q + ~40, and the loads that feed a tile are issued
 // by one producer lane per population instead of 32 lanes each computing an address.
 //
+// Row tiles (ROWS): on an x-periodic lattice with rows of nx <= TX cells a tile is G = TX / nx
+// consecutive rows (lane q of the tile is cell x = q mod nx of row q / nx).  Population i of those
+// rows pulls from G source rows, consecutive in memory except where y or z wraps, so the producer
+// copies each run of them whole with one bulk copy, and the consumer lane reads its pulled value at
+// (x - vx_i) mod nx of its row's stage: the periodic x costs neither split copies nor slack, and
+// every lane holds one stage offset per x velocity, computed once per tile.
+//
 // Stages form a ring of NSTAGE slots per block: tile k of a block goes to stage k % NSTAGE and to
 // consumer group k % groups; every producer warp copies its share of the populations of every
 // tile.  NSTAGE is a multiple of the group count, so each stage is read by one group, and every
@@ -180,11 +187,12 @@ __device__ __forceinline__ int pipe_src_row(int s, int n, int bc) {
 }
 
 // The pipeline of one launch over tiles t = blockIdx.x + k gridDim.x, k = 0, 1, ... < pp.ntiles.
-// `tiles` maps a tile to its lattice: tiles.at(t) gives a TileRef (the lattice's parameters,
-// buffers and status words, the tile's index within that lattice, and whether the lattice steps in
-// this launch); a tile of a lattice that does not step still passes through its stage (no copies,
-// no stores) so that every producer and consumer keeps the stage order.
-template <class L, class S, int TX, bool WALLS, class Tiles>
+// `tiles` maps a tile to its lattice: tiles.member(t) names the lattice and tiles.at(t, member)
+// gives a TileRef (the lattice's parameters, buffers and status words, the tile's index within that
+// lattice, and whether the lattice steps in this launch); a tile of a lattice that does not step
+// still passes through its stage (no copies, no stores) so that every producer and consumer keeps
+// the stage order.
+template <class L, class S, int TX, bool WALLS, bool ROWS, class Tiles>
 __device__ __forceinline__ void pipe_body(const PipeParams& pp, const Tiles& tiles) {
   using T = typename S::T;
   using A = typename S::A;
@@ -241,14 +249,20 @@ __device__ __forceinline__ void pipe_body(const PipeParams& pp, const Tiles& til
         ok = false;
         break;
       }
-      const auto tr = tiles.at(t);
+      const auto tr = tiles.at(t, tiles.member(t));
       const StepParams& p = tr.p;
-      if (lane == 0) mbar_arrive_expect_tx(&full[s], tr.active ? (uint32_t)(mine * Sh::ROW_BYTES) : 0u);
+      // row tiles: rows r0 .. r0 + gt - 1 of the lattice, gt * nx elements per population
+      const int rpt = ROWS ? TX / p.nx : 1;  // rows per tile
+      const int nrows = p.ny * p.nz;
+      const int r0 = ROWS ? tr.lt * rpt : 0;
+      const int gt = ROWS ? min(rpt, nrows - r0) : 1;
+      const uint32_t pop_bytes = ROWS ? (uint32_t)(gt * p.nx * (int)sizeof(T)) : (uint32_t)Sh::ROW_BYTES;
+      if (lane == 0) mbar_arrive_expect_tx(&full[s], tr.active ? (uint32_t)mine * pop_bytes : 0u);
       __syncwarp();
       if (!tr.active) continue;
       const T* __restrict__ src = tr.src;
-      const int segs = (p.nx + TX - 1) / TX;
-      const int seg = tr.lt % segs, row = tr.lt / segs;
+      const int segs = ROWS ? 1 : (p.nx + TX - 1) / TX;
+      const int seg = ROWS ? 0 : tr.lt % segs, row = ROWS ? r0 : tr.lt / segs;
       const int y = row % p.ny, z = row / p.ny;
       const int x0 = seg * TX;
       const bool xperiodic = p.bc[0] == kPeriodic;
@@ -264,6 +278,34 @@ __device__ __forceinline__ void pipe_body(const PipeParams& pp, const Tiles& til
         }
         bulk_g2s(d, src + from, (uint32_t)(n * sizeof(T)), &full[s]);
       };
+      if constexpr (ROWS) {
+        // each run of consecutive source rows of population i with one copy of whole rows
+        for (int i = lane * P + pw; i < L::Q; i += 32 * P) {
+          const char4 v = sv[i];
+          const long long base = (long long)i * p.cells;
+          T* d = st + i * BX;
+          int r = 0, yr = y, zr = z;
+          long long run0 = 0, next = -1;
+          int runlen = 0;
+          for (; r < gt; ++r) {
+            const long long sr = (long long)pipe_src_row(zr - v.z, p.nz, p.bc[2]) * p.ny +
+                                 pipe_src_row(yr - v.y, p.ny, p.bc[1]);
+            if (sr != next) {
+              if (runlen > 0) copy(d + (r - runlen) * p.nx, base + run0 * p.nx, runlen * p.nx);
+              run0 = sr;
+              runlen = 0;
+            }
+            ++runlen;
+            next = sr + 1;
+            if (++yr == p.ny) {
+              yr = 0;
+              ++zr;
+            }
+          }
+          copy(d + (r - runlen) * p.nx, base + run0 * p.nx, runlen * p.nx);
+        }
+        continue;
+      }
       for (int i = lane * P + pw; i < L::Q; i += 32 * P) {
         const char4 v = sv[i];
         const int ys = pipe_src_row(y - v.y, p.ny, p.bc[1]);
@@ -308,56 +350,115 @@ __device__ __forceinline__ void pipe_body(const PipeParams& pp, const Tiles& til
                                 (warp >> 1) * kPipeXchgFloatsPerPair + lane
                           : nullptr;
   int iter = 0;
+  // the lattice of this group's next tile, read one tile ahead (a batch looks it up in memory)
+  int next_member = 0;
+  if (blockIdx.x + (long long)group * G < pp.ntiles) next_member = tiles.member(blockIdx.x + (long long)group * G);
   for (int k = group;; k += pp.groups, ++iter) {
     const long long t = blockIdx.x + (long long)k * G;
     if (t >= pp.ntiles) break;
     const int s = k % pp.nstage;
-    if (!mbar_wait(&full[s], (uint32_t)(k / pp.nstage) & 1u)) {
-      if (lane == 0) atomicAdd(tiles.timeout_word(), 1);
-      return;
+    const auto tr = tiles.at(t, next_member);
+    {
+      const long long tn = t + (long long)pp.groups * G;
+      if (tn < pp.ntiles) next_member = tiles.member(tn);
     }
-    const auto tr = tiles.at(t);
-    if (!tr.active) {
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[s]);
-      continue;
+    // a batch works out the tile's cells and stage offsets (from the member's parameters in
+    // memory) before the wait for the stage, so that their loads overlap it; a single lattice, whose
+    // parameters are kernel arguments, waits first (measured 2% faster)
+    if constexpr (!Tiles::kEarlyGeometry) {
+      if (!mbar_wait(&full[s], (uint32_t)(k / pp.nstage) & 1u)) {
+        if (lane == 0) atomicAdd(tiles.timeout_word(), 1);
+        return;
+      }
     }
     const StepParams& p = tr.p;
     const T* __restrict__ src = tr.src;
     T* __restrict__ dst = tr.dst;
     int* __restrict__ status = tr.status;
-    const int segs = (p.nx + TX - 1) / TX;
-    const int seg = tr.lt % segs, row = tr.lt / segs;
     Cell cl;
-    cl.y = row % p.ny;
-    cl.z = row / p.ny;
-    const int x0 = seg * TX;
-    const int x = x0 + part * 32 + lane;
-    const bool valid = x < p.nx;
-    cl.x = valid ? x : p.nx - 1;
-    cl.c = (cl.z * p.ny + cl.y) * p.nx + cl.x;
-    T* const lb = stage0 + (size_t)s * kStageElems + part * 32 + lane;
+    bool valid;
+    T* lb;
+    // row tiles: the stage offset of lane x's pull for each x velocity vx = j - VMAX_X, wrapped
+    // into its row (unused otherwise)
+    int xo[ROWS ? 2 * L::VMAX_X + 1 : 1];
+    if constexpr (ROWS) {
+      const int rpt = TX / p.nx;  // rows per tile
+      const int q = part * 32 + lane;
+      int r = q / p.nx;
+      const int rl = tr.lt * rpt + r;  // the lattice row
+      valid = r < rpt && rl < p.ny * p.nz;
+      // lanes past the tile's rows read the first cell of the tile (their results are not stored)
+      const int x = valid ? q - r * p.nx : 0;
+      if (!valid) r = 0;
+      const int rv = valid ? rl : tr.lt * rpt;
+      cl.x = x;
+      cl.y = rv % p.ny;
+      cl.z = rv / p.ny;
+      cl.c = rv * p.nx + x;
+      lb = stage0 + (size_t)s * kStageElems + r * p.nx;
+#pragma unroll
+      for (int j = 0; j <= 2 * L::VMAX_X; ++j) {
+        int o = x - (j - L::VMAX_X);
+        o += o < 0 ? p.nx : 0;
+        o -= o >= p.nx ? p.nx : 0;
+        xo[j] = o;
+      }
+    } else {
+      const int segs = (p.nx + TX - 1) / TX;
+      const int seg = tr.lt % segs, row = tr.lt / segs;
+      cl.y = row % p.ny;
+      cl.z = row / p.ny;
+      const int x = seg * TX + part * 32 + lane;
+      valid = x < p.nx;
+      cl.x = valid ? x : p.nx - 1;
+      cl.c = (cl.z * p.ny + cl.y) * p.nx + cl.x;
+      lb = stage0 + (size_t)s * kStageElems + part * 32 + lane;
+      xo[0] = 0;
+    }
+    // the stage element lane x reads for population i
+    auto slot = [&](auto I) -> int {
+      constexpr int i = decltype(I)::value;
+      if constexpr (ROWS) return i * BX + xo[L::VX[i] + L::VMAX_X];
+      else return i * BX + ((-L::VX[i]) % AL + AL) % AL;
+    };
+    if constexpr (Tiles::kEarlyGeometry) {
+      if (!mbar_wait(&full[s], (uint32_t)(k / pp.nstage) & 1u)) {
+        if (lane == 0) atomicAdd(tiles.timeout_word(), 1);
+        return;
+      }
+    }
+    if (!tr.active) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+      continue;
+    }
 
-    // patch what the copies could not express (warp-uniform test), for the populations this warp reads
+    // patch what the copies could not express (warp-uniform test), for the populations this warp
+    // reads: a copy-out or bounce-back x (segment tiles only), the walls
     const bool xperiodic = p.bc[0] == kPeriodic;
-    bool patch = !xperiodic && (x0 < L::VMAX_X || x0 + TX - 1 + L::VMAX_X >= p.nx);
-    if constexpr (WALLS)
-      patch = patch || (p.bc[1] == kBounceBack && (cl.y < L::VMAX_Y || cl.y >= p.ny - L::VMAX_Y)) ||
-              (p.bc[2] == kBounceBack && (cl.z < L::VMAX_Z || cl.z >= p.nz - L::VMAX_Z));
+    bool patch = false;
+    if constexpr (!ROWS) {
+      const int x0 = (tr.lt % ((p.nx + TX - 1) / TX)) * TX;
+      patch = !xperiodic && (x0 < L::VMAX_X || x0 + TX - 1 + L::VMAX_X >= p.nx);
+    }
+    if constexpr (WALLS) {
+      const bool near = (p.bc[1] == kBounceBack && (cl.y < L::VMAX_Y || cl.y >= p.ny - L::VMAX_Y)) ||
+                        (p.bc[2] == kBounceBack && (cl.z < L::VMAX_Z || cl.z >= p.nz - L::VMAX_Z));
+      patch = patch || (ROWS ? __any_sync(0xffffffffu, near) : near);
+    }
     if (patch) {
       static_for<L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int vx = L::VX[i];
-        constexpr int r = ((-vx) % AL + AL) % AL;
         constexpr int ih = i < L::DP_FIRST[KS % L::NDP] || KS == L::NDP ? 0 : 1;  // half of population i
         if (SPLIT && ih != half) return;
         bool need = false;
         if constexpr (WALLS) need = p.has_wall && beyond_wall<L, i>(cl, p);
-        if constexpr (vx != 0) need = need || (!xperiodic && (unsigned)(cl.x - vx) >= (unsigned)p.nx);
+        if constexpr (vx != 0 && !ROWS) need = need || (!xperiodic && (unsigned)(cl.x - vx) >= (unsigned)p.nx);
         if (need) {
           const long long idx = pull_index<L, i, true, WALLS>(cl, p);
           if ((unsigned long long)idx < (unsigned long long)((long long)L::Q * p.cells)) {
-            lb[i * BX + r] = src[idx];
+            lb[slot(I)] = src[idx];
           } else {
             atomicAdd(&status[kStatusBounds], 1);
           }
@@ -368,9 +469,7 @@ __device__ __forceinline__ void pipe_body(const PipeParams& pp, const Tiles& til
     }
 
     auto get = [&](auto I) -> A {
-      constexpr int i = decltype(I)::value;
-      constexpr int r = ((-L::VX[i]) % AL + AL) % AL;
-      const T v = lb[i * BX + r];
+      const T v = lb[slot(I)];
       if constexpr (DEV) return __half2float(v);
       else return (A)v;
     };
@@ -446,11 +545,15 @@ struct TileRef {
 // One lattice: tile t is the lattice's tile t.
 template <class T>
 struct SoloTiles {
+  static constexpr bool kEarlyGeometry = false;
   const StepParams& p;
   const T* src;
   T* dst;
   int* status;
-  __device__ __forceinline__ TileRef<T> at(long long t) const { return TileRef<T>{p, src, dst, status, (int)t, true}; }
+  __device__ __forceinline__ int member(long long) const { return 0; }
+  __device__ __forceinline__ TileRef<T> at(long long t, int) const {
+    return TileRef<T>{p, src, dst, status, (int)t, true};
+  }
   __device__ __forceinline__ int* timeout_word() const { return status + kStatusTimeout; }
   __device__ __forceinline__ int debug() const { return p.debug; }
 };
@@ -460,12 +563,13 @@ struct SoloTiles {
 // steps only while launch < steps_left.
 template <class T>
 struct BatchTiles {
+  static constexpr bool kEarlyGeometry = true;
   const BatchMember* members;
   const int* tile_member;
   int launch;
   int* timeout;
-  __device__ __forceinline__ TileRef<T> at(long long t) const {
-    const int mi = __ldg(&tile_member[t]);
+  __device__ __forceinline__ int member(long long t) const { return __ldg(&tile_member[t]); }
+  __device__ __forceinline__ TileRef<T> at(long long t, int mi) const {
     const BatchMember& m = members[mi];
     const int par = (m.parity0 + launch) & 1;
     return TileRef<T>{m.p, static_cast<const T*>(m.buf[par]), static_cast<T*>(m.buf[par ^ 1]), m.status,
@@ -476,24 +580,24 @@ struct BatchTiles {
 };
 
 // One time step of one lattice.
-template <class L, class S, int TX, bool WALLS>
+template <class L, class S, int TX, bool WALLS, bool ROWS>
 __global__ void __launch_bounds__(kPipeMaxThreads, 1)
     k_step_pipe(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
                 const __grid_constant__ StepParams p, const __grid_constant__ PipeParams pp,
                 int* __restrict__ status) {
   using T = typename S::T;
-  pipe_body<L, S, TX, WALLS>(pp, SoloTiles<T>{p, src, dst, status});
+  pipe_body<L, S, TX, WALLS, ROWS>(pp, SoloTiles<T>{p, src, dst, status});
 }
 
 // One time step of every batch member with steps left (launch index `launch`), persistent over the
 // members' tiles.  A member's result is bitwise that of k_step_pipe on it alone.  Waits that run
 // out are counted in *timeout (the first member's status words).
-template <class L, class S, int TX, bool WALLS>
+template <class L, class S, int TX, bool WALLS, bool ROWS>
 __global__ void __launch_bounds__(kPipeMaxThreads, 1)
     k_step_pipe_batch(const BatchMember* __restrict__ members, const int* __restrict__ tile_member, int launch,
                       const __grid_constant__ PipeParams pp, int* __restrict__ timeout) {
   using T = typename S::T;
-  pipe_body<L, S, TX, WALLS>(pp, BatchTiles<T>{members, tile_member, launch, timeout});
+  pipe_body<L, S, TX, WALLS, ROWS>(pp, BatchTiles<T>{members, tile_member, launch, timeout});
 }
 
 }  // namespace rlb

@@ -19,7 +19,8 @@ STORAGE = {"f64": 0, "f32": 1, "f16dev": 2}
 MAX_VARIANTS = 16
 VARIANT_NAMES = ["registers/scalar", "registers/paired", "registers(168)/scalar", "registers(168)/paired",
                  "pipe tx128 8c8p", "pipe tx128 8c4p", "pipe tx64 8c8p", "pipe tx64 4c4p", "pipe tx128 8c6p",
-                 "pipe tx64 8c4p", "pipe tx128 4c4p", "pipe tx64 2c4p"]
+                 "pipe tx64 8c4p", "pipe tx128 4c4p", "pipe tx64 2c4p", "rows tx128 8c4p", "rows tx128 8c8p",
+                 "rows tx128 4c4p"]
 BC = {"periodic": 0, "copyout": 1, "bounceback": 2}
 
 

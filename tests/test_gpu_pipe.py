@@ -149,7 +149,7 @@ def test_conservation_pipe():
     assert np.max(np.abs(t1 - t0)) <= 2e-6 * np.abs(t0).max()
 
 
-@pytest.mark.parametrize("storage,variant", [("f64", 11), ("f32", 4), ("f32", 6)])
+@pytest.mark.parametrize("storage,variant", [("f64", 11), ("f32", 4), ("f32", 6), ("f32", 12)])
 def test_landau_failure_in_pipe_is_reported(storage, variant):
     """Every cell holding a single population: the pipelined step streams without collision and
     reports RLB_ENONCONV once per cell (float arithmetic: the two warps of a cell stream their own
@@ -170,7 +170,8 @@ def test_landau_failure_in_pipe_is_reported(storage, variant):
 
 
 @pytest.mark.parametrize("storage,pipe,reg,tol", [("f64", 11, 0, 1e-12), ("f32", 4, 3, 1e-5), ("f32", 5, 3, 1e-5),
-                                                  ("f32", 6, 3, 1e-5), ("f16dev", 8, 3, 5e-3)])
+                                                  ("f32", 6, 3, 1e-5), ("f16dev", 8, 3, 5e-3), ("f32", 12, 3, 1e-5),
+                                                  ("f16dev", 13, 3, 5e-3)])
 def test_pipe_equals_register_kernel_with_many_tiles_per_block(storage, pipe, reg, tol):
     """128 x 64 x 64 cells, 6 steps: every block runs dozens of tiles through its stage ring, so
     every stage is reused many times (the register kernels are checked against the oracle in
@@ -193,14 +194,15 @@ def test_pipe_equals_register_kernel_with_many_tiles_per_block(storage, pipe, re
     assert err < tol
 
 
-def test_expired_waits_are_reported_and_the_context_stays_usable():
+@pytest.mark.parametrize("variant", [5, 12])
+def test_expired_waits_are_reported_and_the_context_stays_usable(variant):
     """Testing flag: the pipelined step's producers withhold every tile, so each consumer's bounded
     wait (2 s) runs out; the kernel returns, the next synchronising call reports RLB_ETIMEOUT, and
-    the context keeps working (no GPU fault, no hang)."""
+    the context keeps working (no GPU fault, no hang).  Row segments (5) and row tiles (12)."""
     shape = (8, 8, 128)
     n, T, u = gen.smooth_random_fields(shape, seed=3, vmax=0.3, sigma_lnT=0.1)
-    with RLB(shape, order=3, storage="f32", eta_over_s=0.1, step_variant=5, debug_flags=1) as g:
-        assert g.variant == 5
+    with RLB(shape, order=3, storage="f32", eta_over_s=0.1, step_variant=variant, debug_flags=1) as g:
+        assert g.variant == variant
         g.init(n, T, u)
         f0 = g.populations()
         g.step(1)
@@ -214,3 +216,92 @@ def test_expired_waits_are_reported_and_the_context_stays_usable():
         g.set_populations(f0)
         assert np.array_equal(g.populations(), f0)
         g.moments()
+
+
+# ---- row tiles (variants 12..14): a tile is 128 / nx whole rows of an x-periodic lattice --------
+
+# (shape (nz, ny, nx), bc): rows of 8 to 128 cells, G = 16 .. 1 rows per tile, row counts that leave
+# the last tile short, y and z axes whose wrap splits a tile's source rows into two runs, copy-out
+# and bounce-back y / z
+ROW_CASES = [((7, 13, 128), (0, 0, 0)), ((5, 11, 64), (0, 0, 0)), ((6, 9, 40), (0, 1, 0)),
+             ((9, 7, 32), (0, 0, 1)), ((6, 10, 48), (0, 2, 2)), ((5, 6, 96), (0, 1, 2)), ((4, 5, 8), (0, 0, 0))]
+
+
+@pytest.mark.parametrize("storage,rows,seg", [("f32", 12, 5), ("f32", 13, 4), ("f16dev", 12, 5), ("f16dev", 14, 10)])
+@pytest.mark.parametrize("case", range(len(ROW_CASES)))
+def test_row_tiles_equal_row_segments_bitwise(storage, rows, seg, case):
+    """Row tiles pull every cell's populations from the same source cells as row segments of the
+    same block layout and evaluate the same arithmetic on them, so after 7 steps the populations
+    are bitwise equal (the segment kernel's x wrap is split copies; the row tiles' is a per-lane
+    offset into one copy of the whole rows)."""
+    shape, bc = ROW_CASES[case]
+    n, T, u = gen.smooth_random_fields(shape, seed=40 + case, vmax=0.5, sigma_lnT=0.2)
+    out = {}
+    for v in (rows, seg):
+        with RLB(shape, order=3, bc=bc, storage=storage, eta_over_s=0.1, step_variant=v) as g:
+            if g.variant != v:
+                pytest.skip("variant %d does not exist for %s on %s" % (v, storage, shape))
+            g.init(n, T, u)
+            l0 = g.kernel_launches
+            g.step(7)
+            assert g.kernel_launches - l0 == 7
+            out[v] = g.populations()
+    assert np.array_equal(out[rows], out[seg])
+
+
+@pytest.mark.parametrize("case", range(len(ROW_CASES)))
+def test_row_tiles_f64_match_oracle(case):
+    """Second order, double storage (the row-tile shape whose stages fit double rows: 4 consumer
+    warps, variant 14): populations within 1e-12 of the FP64 oracle after 6 steps, and the fields."""
+    shape, bc = ROW_CASES[case]
+    lat = oracle.read_lattice(2)
+    f0 = near_equilibrium(lat, shape, seed=50 + case, bc=bc)
+    o = oracle.OracleRLB(lat, shape[2], shape[1], shape[0], bc=bc, eta_over_s=0.1)
+    o.set_populations(f0)
+    o.step(6)
+    with RLB(shape, order=2, bc=bc, eta_over_s=0.1, step_variant=14) as g:
+        assert g.variant == 14
+        g.set_populations(f0)
+        l0 = g.kernel_launches
+        g.step(6)
+        assert g.kernel_launches - l0 == 6
+        f = g.populations()
+        m = g.moments()
+    err = pop_err(lat, f, o.f, 2.0)
+    print("rows f64 order 2 %s %s: %.2e" % (shape, bc, err))
+    assert err < 1e-12
+    assert max(field_err(o.moments(), m)) < 1e-12
+
+
+def test_row_tiles_many_tiles_per_block_equal_register_kernel():
+    """64- and 32-cell rows (two and four rows per tile) on lattices with hundreds of tiles per
+    block: float fields of the row tiles against the register kernel with the same float
+    arithmetic (variant 3) after 6 steps, at float rounding."""
+    lat = oracle.read_lattice(3)
+    for shape in ((48, 40, 64), (40, 60, 32)):
+        n, T, u = gen.smooth_random_fields(shape, seed=61, vmax=0.5, sigma_lnT=0.2)
+        out = {}
+        for v in (12, 3):
+            with RLB(shape, order=3, storage="f32", eta_over_s=0.1, step_variant=v) as g:
+                assert g.variant == v
+                g.init(n, T, u)
+                g.step(6)
+                out[v] = g.populations()
+        err = pop_err(lat, out[12], out[3], n.max())
+        print("rows %s vs register: %.2e" % (shape, err))
+        assert err < 1e-5
+
+
+def test_row_tiles_default_and_availability():
+    """Row tiles exist only for an x-periodic lattice with nx <= 128 on 16-byte boundaries (and at
+    least the stencil's x reach); the library picks them by default where their tiles are at least
+    3/4 used, and row segments for wider rows."""
+    for shape, bc, storage, expect in [((8, 8, 64), (0, 0, 0), "f32", True), ((8, 8, 64), (1, 0, 0), "f32", False),
+                                       ((8, 8, 256), (0, 0, 0), "f32", False), ((8, 8, 36), (0, 0, 0), "f32", True),
+                                       ((8, 8, 36), (0, 0, 0), "f16dev", False)]:
+        with RLB(shape, order=3, bc=bc, storage=storage, step_variant=12) as g:
+            assert (g.variant == 12) == expect, (shape, bc, storage, g.variant)
+    with RLB((8, 8, 64), order=3, storage="f32") as g:
+        assert g.variant == 12
+    with RLB((8, 8, 256), order=3, storage="f32") as g:
+        assert 4 <= g.variant < 12
