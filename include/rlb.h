@@ -155,7 +155,7 @@ rlb_status rlb_get_populations(rlb_ctx* ctx, double* f, int on_device);
 rlb_status rlb_set_populations(rlb_ctx* ctx, const double* f, int on_device);
 
 /* Upper bound on the number of step-kernel variants. */
-#define RLB_MAX_VARIANTS 16
+#define RLB_MAX_VARIANTS 24
 
 /* Autotuner: time every step-kernel variant that exists for this context and keep the fastest for
  * later rlb_step calls.  Variants:
@@ -172,6 +172,9 @@ rlb_status rlb_set_populations(rlb_ctx* ctx, const double* f, int on_device);
  *         population and run of consecutive source rows, the periodic x wrapped in shared memory);
  *         only for lattices with a periodic x of at most 128 cells (and at least the stencil's
  *         x reach), nx again a multiple of 16 bytes' worth of populations.
+ *   15..18 row segments (15, 17) and row tiles (16, 18) in three consumer groups of four warps
+ *         per block, 4 (15, 16) or 2 (17, 18) producer warps; float storage relaxes each cell in
+ *         one warp here instead of two.
  * Each variant repeats one step from the current populations into the spare buffer `reps` times, so
  * the state does not change; this is allowed only before the first step after rlb_init /
  * rlb_set_populations (RLB_ESTATE otherwise).  *variant (may be NULL) receives the choice;
@@ -189,8 +192,9 @@ rlb_status rlb_autotune(rlb_ctx* ctx, int reps, int* variant, double ms[RLB_MAX_
  * boundary cells).  With a pipelined variant (4 and up) the members whose rows start on 16-byte
  * boundaries and fill at least 7/8 of the tile lanes go through one launch of the batched
  * pipelined kernel over their row segments; with a row-tile variant (12 and up) the members with a
- * periodic x of at most 128 cells whose row tiles use at least 3/4 of the lanes go through a
- * launch of the row-tile kernel, and the wider members through the row-segment
+ * periodic x of at most 128 cells whose row tiles use at least 3/4 of the lanes and whose rows do
+ * not fill segment tiles (any such member with half storage) go through a launch of the row-tile
+ * kernel, and the other pipelined members through the row-segment
  * kernel of the same block layout; the others (e.g. 1 x 1 x N tubes) run through the register
  * kernels with the variant a context of that storage runs when it has no pipelined one (3 float,
  * 2 half, 0 double; see rlb_batch_member_variant).  Members keep their own buffers, parameters,

@@ -116,7 +116,7 @@ static std::string validate(const rlb_params* p) {
   }
   if (!(p->gamma_thr >= 1.0)) return "gamma_thr must be >= 1";
   if (p->storage == RLB_F16DEV && !(p->n_ref > 0)) return "n_ref must be > 0";
-  if (p->step_variant < -1 || p->step_variant >= RLB_MAX_VARIANTS) return "step_variant must be -1 or 0..15";
+  if (p->step_variant < -1 || p->step_variant >= RLB_MAX_VARIANTS) return "step_variant must be -1 or 0..23";
   if (p->q > 0) {
     int q;
     const int *vel, *lev;
@@ -163,7 +163,7 @@ static int vmax_x(const rlb_ctx* c) { return c->prm.order == 3 ? Quad3::VMAX_X :
 // (pipe_layout) and the tiles.  False if the variant does not exist or the lattice cannot use it
 // (rows must start on 16-byte boundaries; row tiles also need a periodic x of vmax_x .. tx cells).
 static bool pipe_shape(const rlb_ctx* c, int v, PipeParams* pp, int* grid, int* threads, int* smem, int* tx = nullptr,
-                       int* rows = nullptr) {
+                       int* rows = nullptr, int* split = nullptr) {
   PipeLayout lay;
   if (c->sms <= 0 || !pipe_layout(v, c->q, (int)c->elem, c->smem_per_sm, c->smem_optin, &lay)) return false;
   if (c->sp.nx % (16 / (int)c->elem) != 0) return false;
@@ -176,6 +176,7 @@ static bool pipe_shape(const rlb_ctx* c, int v, PipeParams* pp, int* grid, int* 
   if (smem) *smem = lay.smem;
   if (tx) *tx = lay.tx;
   if (rows) *rows = lay.rows;
+  if (split) *split = lay.split;
   return true;
 }
 
@@ -186,25 +187,31 @@ static bool variant_available(const rlb_ctx* c, int v) {
 }
 
 // The variant rlb_step uses unless asked otherwise: the first one that suits the context in an
-// order measured on GB300 (32^3 to 256^3 lattices, third order): row segments, then row tiles for
-// float storage, row tiles first for half storage (whose 128-cell rows step 1.26x faster in row
-// tiles), then the register kernels; the register kernel for double storage (whose step is bound
-// by the double-precision pipe, which the register kernel's 4 warps per scheduler keep busier).
+// order measured on GB300 (32^3 to 256^3 lattices, third order): for float storage one warp per
+// cell in row tiles, then in row segments (0.83 of the copy bandwidth at 256^3), then the two-warp
+// shapes; for half storage row tiles first (whose 128-cell rows step 1.26x faster in row tiles),
+// then row segments in three consumer groups; then the register kernels; the register kernel for double storage (whose step is bound by the
+// double-precision pipe, which the register kernel's 4 warps per scheduler keep busier).
 static int default_variant(const rlb_ctx* c) {
-  static const int pref_f32[] = {5, 12, 4, 13, 8, 6, 9, 7, 3};
-  static const int pref_f16[] = {12, 13, 4, 8, 6, 5, 9, 7, 2};
+  static const int pref_f32[] = {16, 15, 18, 17, 5, 12, 4, 13, 8, 6, 9, 7, 3};
+  static const int pref_f16[] = {12, 16, 15, 13, 4, 8, 6, 5, 9, 7, 2};
   const int* pref = c->prm.storage == RLB_F32 ? pref_f32 : pref_f16;
   const int n = c->prm.storage == RLB_F32 ? (int)(sizeof(pref_f32) / sizeof(int)) : (int)(sizeof(pref_f16) / sizeof(int));
   if (c->prm.storage != RLB_F64)
     for (int k = 0; k < n; ++k) {
-      PipeLayout lay;
-      const bool pipe = pref[k] >= kNumRegVariants;
-      // pipelined shapes only where the lattice's rows fill their tiles (rows_fit_solo for row
-      // tiles, pipe_fits for row segments); a forced variant may still run on any lattice it can take
-      if (pipe && !pipe_layout(pref[k], c->q, (int)c->elem, c->smem_per_sm, c->smem_optin, &lay)) continue;
-      if (pipe && (lay.rows ? !rows_fit_solo(c->sp.nx, lay.tx, (int)c->elem, c->sp.bc[0], vmax_x(c))
-                            : !pipe_fits(c->sp.nx, lay.tx, (int)c->elem)))
-        continue;
+      // pipelined shapes only where the lattice's rows fill their tiles (rows_fit / rows_fit_solo
+      // for row tiles, pipe_fits for row segments); a forced variant may still run on any lattice
+      // it can take
+      if (pref[k] >= kNumRegVariants) {
+        PipeLayout lay;
+        if (!pipe_layout(pref[k], c->q, (int)c->elem, c->smem_per_sm, c->smem_optin, &lay)) continue;
+        const int elem = (int)c->elem;
+        const bool one = elem == 4 && !lay.split;  // one warp per float cell
+        const bool fits = lay.rows ? (one ? rows_fit(c->sp.nx, lay.tx, elem, c->sp.bc[0], vmax_x(c))
+                                          : rows_fit_solo(c->sp.nx, lay.tx, elem, c->sp.bc[0], vmax_x(c)))
+                                   : pipe_fits(c->sp.nx, lay.tx, elem, fill_eighths(lay, elem));
+        if (!fits) continue;
+      }
       if (variant_available(c, pref[k])) return pref[k];
     }
   return kDefaultStepVariant;
@@ -217,12 +224,12 @@ static rlb_status check_launch(rlb_ctx* c, cudaError_t e, const char* what);
 static rlb_status launch_step(rlb_ctx* c, int v) {
   if (v >= kNumRegVariants) {
     PipeParams pp;
-    int grid = 0, threads = 0, smem = 0, tx = 0, rows = 0;
-    if (!pipe_shape(c, v, &pp, &grid, &threads, &smem, &tx, &rows))
+    int grid = 0, threads = 0, smem = 0, tx = 0, rows = 0, split = 0;
+    if (!pipe_shape(c, v, &pp, &grid, &threads, &smem, &tx, &rows, &split))
       return fail(c, RLB_EINVAL, "step variant not available");
     return check_launch(c,
                         c->launch->pipe_step(c->buf[c->cur], c->buf[1 - c->cur], c->sp, pp, c->status, tx, rows,
-                                             grid, threads, smem, c->stream),
+                                             split, grid, threads, smem, c->stream),
                         "pipelined step kernel");
   }
   rlb_status st = check_launch(

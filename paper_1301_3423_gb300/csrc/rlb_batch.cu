@@ -118,12 +118,17 @@ static bool variant_exists(const rlb_batch* b, int v, PipeLayout* lay = nullptr)
 }
 
 // How a member runs under step variant v: 2 row tiles, 1 row segments (pipelined kernel), 0 the
-// register kernels (variant v itself, or reg_fallback for a pipelined v).
+// register kernels (variant v itself, or reg_fallback for a pipelined v).  Rows that fill segment
+// tiles go to row tiles too, except with two warps per float cell (measured on GB300 at 128^3:
+// one warp per float cell 1.13x faster in row tiles, half storage 1.26x; two warps per float cell
+// 1.04x faster in segments).
 static int member_mode(const rlb_batch* b, const StepParams& p, int v, const PipeLayout& lay) {
   if (v < kNumRegVariants) return 0;
   const int vmax = b->order == 3 ? Quad3::VMAX_X : Quad2::VMAX_X;
-  if (lay.rows && rows_fit(p.nx, lay.tx, elem_of(b->storage), p.bc[0], vmax)) return 2;
-  return pipe_fits(p.nx, lay.tx, elem_of(b->storage)) ? 1 : 0;
+  const int elem = elem_of(b->storage);
+  const bool seg = pipe_fits(p.nx, lay.tx, elem, fill_eighths(lay, elem));
+  if (lay.rows && rows_fit(p.nx, lay.tx, elem, p.bc[0], vmax) && (!seg || !lay.split)) return 2;
+  return seg ? 1 : 0;
 }
 
 // The row-segment variant with the block layout of row-tile variant v (the shape the batch runs its
@@ -135,7 +140,7 @@ static int segment_sibling(int v) {
   for (int k = 0; k < kNumPipeConfigs; ++k) {
     const PipeConfig& d = kPipeConfigs[k];
     if (!d.rows && d.tx == c.tx && d.cons_warps == c.cons_warps && d.ctas_per_sm == c.ctas_per_sm &&
-        d.producers == c.producers)
+        d.producers == c.producers && d.split == c.split)
       return kNumRegVariants + k;
   }
   return -1;
@@ -315,7 +320,8 @@ static rlb_status enqueue_step(rlb_batch* b, int k, int variant, int* counters) 
     const PipeParams pp{b->lay.producers, ntiles, b->lay.nstage, b->lay.groups};
     const int grid = std::min(b->sms * b->lay.ctas_per_sm, ntiles);
     e = b->launch->pipe_batch_step(b->d_members, rows ? b->d_rtile_tm : b->d_pipe_tm, k, pp, b->pipe_timeout,
-                                   b->lay.tx, rows, b->pipe_walls, grid, b->lay.threads, b->lay.smem, b->stream);
+                                   b->lay.tx, rows, b->lay.split, b->pipe_walls, grid, b->lay.threads, b->lay.smem,
+                                   b->stream);
     ++b->launches;
     if (e != cudaSuccess) return bfail(b, RLB_ECUDA, std::string("batched pipelined step: ") + cudaGetErrorString(e));
   }

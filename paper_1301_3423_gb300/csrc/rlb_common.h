@@ -21,13 +21,18 @@ struct PipeConfig {
   int producers;    // producer warps per block (each copies every producers-th population of every tile)
   int rows;         // 0: a tile is a TX-cell segment of one row; 1: a tile is TX / nx whole rows of
                     // an x-periodic lattice with nx <= TX ("row tiles", one copy per population)
+  int split;        // float storage: 1 = two warps per cell (each half the populations), 0 = one;
+                    // other storages always take one warp per cell (the flag makes no difference)
 };
 // A block's stage count is a multiple of its consumer-group count, so that every stage is read by
 // one consumer group, in the order of the stage's uses like every producer: a parity wait then
-// always refers to the phase it means.
-constexpr PipeConfig kPipeConfigs[] = {{128, 8, 1, 8, 0}, {128, 8, 1, 4, 0}, {64, 8, 1, 8, 0}, {64, 4, 1, 4, 0},
-                                       {128, 8, 1, 6, 0}, {64, 8, 1, 4, 0}, {128, 4, 1, 4, 0}, {64, 2, 1, 4, 0},
-                                       {128, 8, 1, 4, 1}, {128, 8, 1, 8, 1}, {128, 4, 1, 4, 1}};
+// always refers to the phase it means.  With as many stages as groups each group refills its one
+// stage while the other groups compute.
+constexpr PipeConfig kPipeConfigs[] = {
+    {128, 8, 1, 8, 0, 1}, {128, 8, 1, 4, 0, 1},  {64, 8, 1, 8, 0, 1},  {64, 4, 1, 4, 0, 1},
+    {128, 8, 1, 6, 0, 1}, {64, 8, 1, 4, 0, 1},   {128, 4, 1, 4, 0, 1}, {64, 2, 1, 4, 0, 1},
+    {128, 8, 1, 4, 1, 1}, {128, 8, 1, 8, 1, 1},  {128, 4, 1, 4, 1, 1}, {128, 12, 1, 4, 0, 0},
+    {128, 12, 1, 4, 1, 0}, {128, 12, 1, 2, 0, 0}, {128, 12, 1, 2, 1, 0}};
 constexpr int kNumPipeConfigs = sizeof(kPipeConfigs) / sizeof(kPipeConfigs[0]);
 constexpr int kNumVariantsTotal = kNumRegVariants + kNumPipeConfigs;
 constexpr int kPipeMaxStages = 16;

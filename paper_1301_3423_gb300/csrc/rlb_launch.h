@@ -30,32 +30,36 @@ struct Launchers {
   // resident blocks per SM of the batched step for a variant
   int (*batch_blocks_per_sm)(int variant);
   // one time step of the pipelined kernel with tile width tx (64 or 128), row tiles if rows != 0
-  // (tx 128 only)
+  // (tx 128 only), float cells split between two warps if split != 0 (float storage)
   cudaError_t (*pipe_step)(const void* src, void* dst, const StepParams& p, const PipeParams& pp, int* status, int tx,
-                           int rows, int grid, int threads, int smem, cudaStream_t s);
+                           int rows, int split, int grid, int threads, int smem, cudaStream_t s);
   // one time step of the batched pipelined kernel (launch index `launch`) over the members' tiles;
   // walls != 0 selects the kernel with the bounce-back patch
   cudaError_t (*pipe_batch_step)(const BatchMember* members, const int* tile_member, int launch, const PipeParams& pp,
-                                 int* timeout, int tx, int rows, int walls, int grid, int threads, int smem,
+                                 int* timeout, int tx, int rows, int split, int walls, int grid, int threads, int smem,
                                  cudaStream_t s);
 };
 
 // Block layout of pipelined variant v (>= kNumRegVariants) for q populations of `elem` bytes:
 // stages (the largest multiple of the consumer-group count that fits the shared memory of one
-// block, at least two per group), groups, threads and shared-memory bytes.  False if the variant
+// block, at least one per group and two in all), groups, threads and shared-memory bytes.  False if the variant
 // does not exist for this storage.
 struct PipeLayout {
-  int tx, nstage, groups, producers, threads, smem, ctas_per_sm, rows;
+  int tx, nstage, groups, producers, threads, smem, ctas_per_sm, rows, split;
 };
 
 // A lattice row of nx cells suits tiles of tx cells when its rows start on 16-byte boundaries and
-// the tiles' lanes are at least 7/8 used (a 96-cell row in 128-cell tiles leaves 1/4 idle and ran
-// slower than the register kernel).
-inline bool pipe_fits(int nx, int tx, int elem) {
+// the tiles' lanes are at least `eighths` / 8 used.  Two warps per float cell want 7/8 (a 96-cell
+// row in 128-cell tiles leaves 1/4 idle and ran slower than the register kernel); one warp per
+// float cell 3/4 (200-cell rows in 128-cell tiles ran faster than the register kernel).
+inline bool pipe_fits(int nx, int tx, int elem, int eighths = 7) {
   if (nx % (16 / elem) != 0) return false;
   const long long used = (long long)((nx + tx - 1) / tx) * tx;
-  return 8LL * nx >= 7 * used;
+  return 8LL * nx >= eighths * used;
 }
+
+// The fill rule of a layout: 3/4 for one warp per float cell, 7/8 otherwise.
+inline int fill_eighths(const PipeLayout& lay, int elem) { return (elem == 4 && !lay.split) ? 6 : 7; }
 
 // Row tiles of tx cells can take a lattice whose x axis is periodic and at least the stencil reach
 // vmax_x long (one wrap per pull), with nx <= tx cells per row starting on 16-byte boundaries.
@@ -70,10 +74,12 @@ inline bool rows_fit(int nx, int tx, int elem, int bc_x, int vmax_x) {
   return rows_possible(nx, tx, elem, bc_x, vmax_x) && 4 * (tx / nx) * nx >= 3 * tx;
 }
 
-// A single lattice's rule: several rows per tile (G >= 2) at 3/4 of the lanes, or one row that
-// fills the tile (measured on GB300 alone: 32-, 48- and 64-cell rows as fast as or faster than the
-// register kernels, 128-cell rows as fast as row segments with float storage and 1.26x faster with
-// half storage, while one 96-cell row per tile ran 1.4x slower than the register kernels).
+// A single lattice's rule for layouts with two warps per float cell and half storage: several
+// rows per tile (G >= 2) at 3/4 of the lanes, or one row that fills the tile (measured on GB300
+// alone: 32-, 48- and 64-cell rows as fast as or faster than the register kernels, 128-cell rows
+// as fast as row segments with float storage and 1.26x faster with half storage, while one 96-cell
+// row per tile ran 1.4x slower than the register kernels).  One warp per float cell takes rows_fit
+// (a 96-cell row per tile ran 1.07x faster than the register kernels).
 inline bool rows_fit_solo(int nx, int tx, int elem, int bc_x, int vmax_x) {
   if (!rows_fit(nx, tx, elem, bc_x, vmax_x)) return false;
   return tx / nx >= 2 || nx == tx;
@@ -95,7 +101,7 @@ inline bool pipe_layout(int v, int q, int elem, int smem_per_sm, int smem_optin,
   const long long stage = (long long)q * (cf.tx + A) * elem;
   long long budget = smem_per_sm / cf.ctas_per_sm - 1024;
   if (budget > smem_optin) budget = smem_optin;
-  const bool split = elem == 4;  // float storage: two consumer warps per cell
+  const bool split = elem == 4 && cf.split;  // float storage: two consumer warps per cell
   const int wpt = cf.tx / 32 * (split ? 2 : 1);
   const int groups = cf.cons_warps / wpt;
   if (groups < 1 || cf.cons_warps % wpt != 0 || cf.producers < 1 || cf.producers > q) return false;
@@ -106,9 +112,9 @@ inline bool pipe_layout(int v, int q, int elem, int smem_per_sm, int smem_optin,
   long long fit = (budget - kPipeHeaderBytes - xchg) / stage;
   if (fit > kPipeMaxStages) fit = kPipeMaxStages;
   const int nstage = (int)(fit / groups * groups);
-  if (nstage < 2 * groups) return false;
+  if (nstage < groups || nstage < 2) return false;
   if (out) *out = PipeLayout{cf.tx, nstage, groups, cf.producers, (cf.cons_warps + cf.producers) * 32,
-                             (int)(kPipeHeaderBytes + nstage * stage + xchg), cf.ctas_per_sm, cf.rows};
+                             (int)(kPipeHeaderBytes + nstage * stage + xchg), cf.ctas_per_sm, cf.rows, split};
   return true;
 }
 

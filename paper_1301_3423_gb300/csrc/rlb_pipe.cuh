@@ -192,15 +192,15 @@ __device__ __forceinline__ int pipe_src_row(int s, int n, int bc) {
 // lattice, and whether the lattice steps in this launch); a tile of a lattice that does not step
 // still passes through its stage (no copies, no stores) so that every producer and consumer keeps
 // the stage order.
-template <class L, class S, int TX, bool WALLS, bool ROWS, class Tiles>
+template <class L, class S, int TX, bool WALLS, bool ROWS, bool ONEWARP, class Tiles>
 __device__ __forceinline__ void pipe_body(const PipeParams& pp, const Tiles& tiles) {
   using T = typename S::T;
   using A = typename S::A;
   using Sh = PipeShape<S, TX>;
   constexpr bool PACKED = std::is_same<A, float>::value;
-  // float storage: two warps per cell (see the consumer section); half storage, whose stages are
-  // half the size, runs more consumer groups instead
-  constexpr bool SPLIT = std::is_same<S, StoreF32>::value;
+  // float storage: two warps per cell (see the consumer section) unless ONEWARP; half storage,
+  // whose stages are half the size, runs more consumer groups instead
+  constexpr bool SPLIT = std::is_same<S, StoreF32>::value && !ONEWARP;
   constexpr int HALVES = SPLIT ? 2 : 1;
   constexpr int KS = SPLIT ? DpSplit<L>::value : L::NDP;
   constexpr int BX = Sh::BX, AL = Sh::A, WPT = TX / 32 * HALVES;
@@ -427,7 +427,10 @@ __device__ __forceinline__ void pipe_body(const PipeParams& pp, const Tiles& til
         return;
       }
     }
-    if (!tr.active) {
+    // a lattice that does not step, or a warp none of whose lanes holds a cell of the tile (the
+    // last part of a tile of 96-cell rows, a ragged row end): release the stage and leave the issue
+    // slots to the other warps (both warps of a float pair skip together)
+    if (!tr.active || !__any_sync(0xffffffffu, valid)) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
       continue;
@@ -580,24 +583,24 @@ struct BatchTiles {
 };
 
 // One time step of one lattice.
-template <class L, class S, int TX, bool WALLS, bool ROWS>
+template <class L, class S, int TX, bool WALLS, bool ROWS, bool ONEWARP>
 __global__ void __launch_bounds__(kPipeMaxThreads, 1)
     k_step_pipe(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
                 const __grid_constant__ StepParams p, const __grid_constant__ PipeParams pp,
                 int* __restrict__ status) {
   using T = typename S::T;
-  pipe_body<L, S, TX, WALLS, ROWS>(pp, SoloTiles<T>{p, src, dst, status});
+  pipe_body<L, S, TX, WALLS, ROWS, ONEWARP>(pp, SoloTiles<T>{p, src, dst, status});
 }
 
 // One time step of every batch member with steps left (launch index `launch`), persistent over the
 // members' tiles.  A member's result is bitwise that of k_step_pipe on it alone.  Waits that run
 // out are counted in *timeout (the first member's status words).
-template <class L, class S, int TX, bool WALLS, bool ROWS>
+template <class L, class S, int TX, bool WALLS, bool ROWS, bool ONEWARP>
 __global__ void __launch_bounds__(kPipeMaxThreads, 1)
     k_step_pipe_batch(const BatchMember* __restrict__ members, const int* __restrict__ tile_member, int launch,
                       const __grid_constant__ PipeParams pp, int* __restrict__ timeout) {
   using T = typename S::T;
-  pipe_body<L, S, TX, WALLS, ROWS>(pp, BatchTiles<T>{members, tile_member, launch, timeout});
+  pipe_body<L, S, TX, WALLS, ROWS, ONEWARP>(pp, BatchTiles<T>{members, tile_member, launch, timeout});
 }
 
 }  // namespace rlb

@@ -16,11 +16,12 @@ RLB_OK, RLB_EINVAL, RLB_ENOMEM, RLB_ECUDA, RLB_ENONCONV, RLB_ENAN, RLB_ETIMEOUT,
 STATUS_NAMES = ["RLB_OK", "RLB_EINVAL", "RLB_ENOMEM", "RLB_ECUDA", "RLB_ENONCONV", "RLB_ENAN", "RLB_ETIMEOUT",
                 "RLB_ESTATE"]
 STORAGE = {"f64": 0, "f32": 1, "f16dev": 2}
-MAX_VARIANTS = 16
+MAX_VARIANTS = 24
 VARIANT_NAMES = ["registers/scalar", "registers/paired", "registers(168)/scalar", "registers(168)/paired",
                  "pipe tx128 8c8p", "pipe tx128 8c4p", "pipe tx64 8c8p", "pipe tx64 4c4p", "pipe tx128 8c6p",
                  "pipe tx64 8c4p", "pipe tx128 4c4p", "pipe tx64 2c4p", "rows tx128 8c4p", "rows tx128 8c8p",
-                 "rows tx128 4c4p"]
+                 "rows tx128 4c4p", "pipe tx128 12c4p 1w", "rows tx128 12c4p 1w", "pipe tx128 12c2p 1w",
+                 "rows tx128 12c2p 1w"]
 BC = {"periodic": 0, "copyout": 1, "bounceback": 2}
 
 

@@ -62,7 +62,7 @@ def test_bytes_required():
 
 
 @pytest.mark.parametrize("bad", [dict(order=4), dict(nx=0), dict(storage=7), dict(eta_over_s=-1.0),
-                                 dict(gamma_thr=0.5), dict(bc=(0, 3, 0)), dict(step_variant=16)])
+                                 dict(gamma_thr=0.5), dict(bc=(0, 3, 0)), dict(step_variant=24)])
 def test_create_rejects_invalid_parameters(bad):
     """Validation happens on the host before any device call."""
     kw = dict(shape=(4, 4, 4))

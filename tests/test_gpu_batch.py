@@ -51,16 +51,17 @@ def make(order, storage, variant, k, stream=None):
                                                    (3, "f16dev", 0), (3, "f16dev", 3),
                                                    (3, "f32", 5), (3, "f32", 4), (2, "f32", 5), (3, "f16dev", 4),
                                                    (3, "f64", 11), (3, "f32", 12), (3, "f32", 13), (2, "f32", 12),
-                                                   (3, "f16dev", 13), (2, "f64", 14)])
+                                                   (3, "f16dev", 13), (2, "f64", 14), (3, "f32", 15), (3, "f32", 16),
+                                                   (3, "f16dev", 16), (2, "f32", 18)])
 @pytest.mark.parametrize("graph", [True, False])
 def test_batched_members_equal_solo_runs(order, storage, variant, graph):
     """Variants 0-3: every member on the register kernels.  Variants 4 to 11: members whose rows
     fill the pipelined tiles (the 128-cell rows here) on the batched pipelined kernel, the others
     (1 x 1 x N tubes, rows of 7 to 192 cells) on the register kernel a context of that storage runs
-    alone.  Row-tile variants (12 and up): the x-periodic members with rows of 32 to 128 cells on
-    the row-tile kernel, the 128-cell rows with bounce-back x on the row-segment kernel of the same
-    layout, the rest on the register kernel.  Each member equals its solo run with the variant the
-    batch reports."""
+    alone.  Row-tile variants: the x-periodic members with rows of 32 and 40 cells (and 128 unless
+    a float cell takes two warps) on the row-tile kernel, the other 128-cell rows on the
+    row-segment kernel of the same layout, the rest on the register kernel.  Each member equals its
+    solo run with the variant the batch reports."""
     ctxs = [make(order, storage, variant, k) for k in range(len(MEMBERS))]
     with Batch(order, storage) as b:
         if variant >= 0:
@@ -69,8 +70,9 @@ def test_batched_members_equal_solo_runs(order, storage, variant, graph):
         used = [b.member_variant(s) for s in slots]  # the variant each member runs with in the batch
         if variant >= 4:
             assert any(v == variant for v in used) and any(v != variant for v in used)
-        if variant >= 12:
-            assert any(4 <= v < 12 for v in used)  # a row-segment member beside the row-tile ones
+        if rlbmod.VARIANT_NAMES[max(variant, 0)].startswith("rows"):
+            # a row-segment member beside the row-tile ones
+            assert any(v >= 4 and rlbmod.VARIANT_NAMES[v].startswith("pipe") for v in used)
         solo = []
         for k in range(len(MEMBERS)):
             ctx, steps = make(order, storage, used[k] if variant >= 0 else variant, k)

@@ -24,7 +24,7 @@ PIPE = list(range(4, len(rlbmod.VARIANT_NAMES)))
 
 @pytest.mark.parametrize("order", [3, 2])
 @pytest.mark.parametrize("bc", ["periodic", "copyout_z", "copyout_xy", "walls_xz", "box"])
-@pytest.mark.parametrize("variant", [11, 7, 10])
+@pytest.mark.parametrize("variant", [11, 7, 10, 15])
 def test_f64_pipe_matches_oracle(order, bc, variant):
     """Double storage, 72 x 13 x 11 cells, with 64-cell tiles and 2 consumer warps (the shape whose
     stages fit double rows of both orders), 64-cell tiles with 4 consumer warps and 128-cell tiles
@@ -149,7 +149,8 @@ def test_conservation_pipe():
     assert np.max(np.abs(t1 - t0)) <= 2e-6 * np.abs(t0).max()
 
 
-@pytest.mark.parametrize("storage,variant", [("f64", 11), ("f32", 4), ("f32", 6), ("f32", 12)])
+@pytest.mark.parametrize("storage,variant", [("f64", 11), ("f32", 4), ("f32", 6), ("f32", 12), ("f32", 15),
+                                             ("f32", 16)])
 def test_landau_failure_in_pipe_is_reported(storage, variant):
     """Every cell holding a single population: the pipelined step streams without collision and
     reports RLB_ENONCONV once per cell (float arithmetic: the two warps of a cell stream their own
@@ -171,7 +172,8 @@ def test_landau_failure_in_pipe_is_reported(storage, variant):
 
 @pytest.mark.parametrize("storage,pipe,reg,tol", [("f64", 11, 0, 1e-12), ("f32", 4, 3, 1e-5), ("f32", 5, 3, 1e-5),
                                                   ("f32", 6, 3, 1e-5), ("f16dev", 8, 3, 5e-3), ("f32", 12, 3, 1e-5),
-                                                  ("f16dev", 13, 3, 5e-3)])
+                                                  ("f16dev", 13, 3, 5e-3), ("f32", 15, 3, 1e-5), ("f32", 16, 3, 1e-5),
+                                                  ("f32", 17, 3, 1e-5), ("f16dev", 16, 3, 5e-3)])
 def test_pipe_equals_register_kernel_with_many_tiles_per_block(storage, pipe, reg, tol):
     """128 x 64 x 64 cells, 6 steps: every block runs dozens of tiles through its stage ring, so
     every stage is reused many times (the register kernels are checked against the oracle in
@@ -194,11 +196,12 @@ def test_pipe_equals_register_kernel_with_many_tiles_per_block(storage, pipe, re
     assert err < tol
 
 
-@pytest.mark.parametrize("variant", [5, 12])
+@pytest.mark.parametrize("variant", [5, 12, 15])
 def test_expired_waits_are_reported_and_the_context_stays_usable(variant):
     """Testing flag: the pipelined step's producers withhold every tile, so each consumer's bounded
     wait (2 s) runs out; the kernel returns, the next synchronising call reports RLB_ETIMEOUT, and
-    the context keeps working (no GPU fault, no hang).  Row segments (5) and row tiles (12)."""
+    the context keeps working (no GPU fault, no hang).  Row segments (5), row tiles (12), three
+    consumer groups with one stage each (15)."""
     shape = (8, 8, 128)
     n, T, u = gen.smooth_random_fields(shape, seed=3, vmax=0.3, sigma_lnT=0.1)
     with RLB(shape, order=3, storage="f32", eta_over_s=0.1, step_variant=variant, debug_flags=1) as g:
@@ -227,7 +230,8 @@ ROW_CASES = [((7, 13, 128), (0, 0, 0)), ((5, 11, 64), (0, 0, 0)), ((6, 9, 40), (
              ((9, 7, 32), (0, 0, 1)), ((6, 10, 48), (0, 2, 2)), ((5, 6, 96), (0, 1, 2)), ((4, 5, 8), (0, 0, 0))]
 
 
-@pytest.mark.parametrize("storage,rows,seg", [("f32", 12, 5), ("f32", 13, 4), ("f16dev", 12, 5), ("f16dev", 14, 10)])
+@pytest.mark.parametrize("storage,rows,seg", [("f32", 12, 5), ("f32", 13, 4), ("f32", 16, 15), ("f32", 18, 17),
+                                              ("f16dev", 12, 5), ("f16dev", 14, 10), ("f16dev", 16, 15)])
 @pytest.mark.parametrize("case", range(len(ROW_CASES)))
 def test_row_tiles_equal_row_segments_bitwise(storage, rows, seg, case):
     """Row tiles pull every cell's populations from the same source cells as row segments of the
@@ -302,6 +306,6 @@ def test_row_tiles_default_and_availability():
         with RLB(shape, order=3, bc=bc, storage=storage, step_variant=12) as g:
             assert (g.variant == 12) == expect, (shape, bc, storage, g.variant)
     with RLB((8, 8, 64), order=3, storage="f32") as g:
-        assert g.variant == 12
+        assert g.variant == 16  # one warp per cell, row tiles
     with RLB((8, 8, 256), order=3, storage="f32") as g:
-        assert 4 <= g.variant < 12
+        assert g.variant == 15  # one warp per cell, row segments
