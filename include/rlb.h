@@ -121,8 +121,9 @@ rlb_status rlb_create(const rlb_params* p, rlb_ctx** out);
 
 /* Set every population to the discrete equilibrium f_i^eq(n, T, U) (Eq. (eq:disc1)) of the given
  * fields, U = gamma (1, u): n, T double[cells], u double[3][cells] (u_x, u_y, u_z, |u| < 1).
- * on_device = 0: host pointers (copied before return); 1: device pointers.  Resets the step
- * counter to 0.  Errors: RLB_EINVAL (null pointer; invalid values are reported as RLB_EINVAL by
+ * on_device = 0: host pointers, read before return (page-locked arrays, e.g. from cudaHostAlloc
+ * or cudaHostRegister, are read by the init kernel in place over the CPU-GPU link; pageable ones
+ * are copied through a device staging buffer); 1: device pointers.  Resets the step counter to 0.  Errors: RLB_EINVAL (null pointer; invalid values are reported as RLB_EINVAL by
  * the next synchronising call), RLB_ECUDA. */
 rlb_status rlb_init(rlb_ctx* ctx, const double* n, const double* T, const double* u, int on_device);
 
@@ -135,7 +136,9 @@ rlb_status rlb_step(rlb_ctx* ctx, long nsteps);
  * double[cells], U double[4][cells] (U^0..U^3), and totals[5] = sum over cells of N^0, T^00,
  * T^0x, T^0y, T^0z (the conserved densities of Eqs. (eq:conser1), (eq:conser2)), summed in double
  * in a fixed order.  Any output pointer may be NULL.  on_device = 1: n, eps, U are device
- * pointers (totals is always host).  Synchronises the stream.  Errors, from this call or from
+ * pointers (totals is always host); 0: host pointers (when n, eps and U are all page-locked the
+ * fields kernel writes them in place, otherwise they are copied out of a device buffer).
+ * Synchronises the stream.  Errors, from this call or from
  * enqueued work since the last synchronising call: RLB_ENAN (cells whose populations are not
  * finite), RLB_ENONCONV (cells without a Landau frame, here or in a step; their fields are NaN),
  * RLB_EINVAL (invalid initial fields given to rlb_init), RLB_ETIMEOUT (a bounded device-side wait

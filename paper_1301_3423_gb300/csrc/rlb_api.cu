@@ -424,11 +424,41 @@ static rlb_status ensure_copy_stream(rlb_ctx* c) {
   return RLB_OK;
 }
 
+// The device address of host array p[0 .. count) when the whole array is page-locked host memory
+// the device can address (cudaHostAlloc, cudaHostRegister): its first and last elements are both
+// mapped, at device addresses as far apart as the host addresses.  nullptr otherwise (pageable
+// memory, or an array only partly registered), and then the data go through copies.
+static double* mapped_host(const double* p, size_t count) {
+  if (!p || count == 0) return nullptr;
+  cudaPointerAttributes a{}, b{};
+  const double* last = p + (count - 1);
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess || cudaPointerGetAttributes(&b, last) != cudaSuccess) {
+    cudaGetLastError();  // an address CUDA does not know: not an error of this context
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer || !b.devicePointer)
+    return nullptr;
+  if ((const char*)b.devicePointer - (const char*)a.devicePointer != (const char*)last - (const char*)p)
+    return nullptr;
+  return static_cast<double*>(a.devicePointer);
+}
+
 extern "C" rlb_status rlb_init(rlb_ctx* c, const double* n, const double* T, const double* u, int on_device) {
   if (!c) return RLB_EINVAL;
   if (!n || !T || !u) return fail(c, RLB_EINVAL, "rlb_init: null field pointer");
   rlb_status st = RLB_OK;
-  if (on_device) {
+  const size_t ncell = (size_t)c->cells;
+  const double* hn = on_device ? nullptr : mapped_host(n, ncell);
+  const double* hT = on_device ? nullptr : mapped_host(T, ncell);
+  const double* hu = on_device ? nullptr : mapped_host(u, 3 * ncell);
+  if (hn && hT && hu) {
+    // page-locked host fields: the init kernel reads them where they are (over the CPU-GPU link),
+    // one launch, no staging copies; the host arrays are free again once the call returns
+    st = check_launch(c, c->launch->init(hn, hT, hu, c->buf[c->cur], c->sp, c->status, 0, c->cells, c->stream),
+                      "init kernel");
+    if (st != RLB_OK) return st;
+    RLB_CUDA(c, cudaStreamSynchronize(c->stream));
+  } else if (on_device) {
     st = check_launch(c, c->launch->init(n, T, u, c->buf[c->cur], c->sp, c->status, 0, c->cells, c->stream),
                       "init kernel");
     if (st != RLB_OK) return st;
@@ -519,8 +549,19 @@ extern "C" rlb_status rlb_moments(rlb_ctx* c, double* n, double* eps, double* U,
   const void* src = pull ? c->buf[1 - c->cur] : c->buf[c->cur];
   const size_t cells = (size_t)c->cells;
   rlb_status st = RLB_OK;
-  if (on_device || (!n && !eps && !U)) {
-    st = check_launch(c, c->launch->fields(src, c->sp, c->fields, c->partial, c->status, pull, 0, c->fblocks, c->stream),
+  const FieldOut staged{{c->fields, c->fields + cells, c->fields + 2 * cells, c->fields + 3 * cells,
+                        c->fields + 4 * cells, c->fields + 5 * cells}};
+  double* hn = (on_device || !n) ? nullptr : mapped_host(n, cells);
+  double* he = (on_device || !eps) ? nullptr : mapped_host(eps, cells);
+  double* hU = (on_device || !U) ? nullptr : mapped_host(U, 4 * cells);
+  if (hn && he && hU) {
+    // page-locked host outputs: the fields kernel writes them where they are, one launch
+    const FieldOut host{{hn, he, hU, hU + cells, hU + 2 * cells, hU + 3 * cells}};
+    st = check_launch(c, c->launch->fields(src, c->sp, host, c->partial, c->status, pull, 0, c->fblocks, c->stream),
+                      "fields kernel");
+    if (st != RLB_OK) return st;
+  } else if (on_device || (!n && !eps && !U)) {
+    st = check_launch(c, c->launch->fields(src, c->sp, staged, c->partial, c->status, pull, 0, c->fblocks, c->stream),
                       "fields kernel");
     if (st != RLB_OK) return st;
     const size_t cb = cells * sizeof(double);
@@ -536,7 +577,7 @@ extern "C" rlb_status rlb_moments(rlb_ctx* c, double* n, double* eps, double* U,
     for (int j = 0; j < kChunks; ++j) {
       const int b0 = std::min(c->fblocks, j * per_blocks), b1 = std::min(c->fblocks, (j + 1) * per_blocks);
       if (b0 >= b1) break;
-      st = check_launch(c, c->launch->fields(src, c->sp, c->fields, c->partial, c->status, pull, b0, b1, c->stream),
+      st = check_launch(c, c->launch->fields(src, c->sp, staged, c->partial, c->status, pull, b0, b1, c->stream),
                         "fields kernel");
       if (st != RLB_OK) return st;
       RLB_CUDA(c, cudaEventRecord(c->ev_chunk[j], c->stream));

@@ -105,6 +105,12 @@ struct PipeParams {
   int groups;     // consumer groups per block (TX / 32 warps each, twice that for float storage)
 };
 
+// Output arrays of the fields kernel: n, eps, U0, U1, U2, U3, one value per cell each (device
+// memory, or host memory the device can address).
+struct FieldOut {
+  double* f[6];
+};
+
 // One lattice of a batched step (see k_step_batch).
 struct BatchMember {
   StepParams p;

@@ -44,7 +44,7 @@ int batch_blocks_per_sm(int variant) {
   return RLB_VFN(occupancy, 0)();
 }
 
-cudaError_t fields(const void* src, const StepParams& p, double* f, double* partial, int* status, bool pull,
+cudaError_t fields(const void* src, const StepParams& p, const FieldOut& f, double* partial, int* status, bool pull,
                    int block0, int block1, cudaStream_t s) {
   const int blocks = block1 - block0;
   if (blocks <= 0) return cudaSuccess;

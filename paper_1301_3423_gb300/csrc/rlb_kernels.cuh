@@ -1122,13 +1122,13 @@ __device__ __forceinline__ Mom<double> moments_pd(GetF&& getf, double c) {
 //   PULL = true : the pre-collision populations pulled from the previous state (GENERAL: modulo
 //                 wrap, for periodic axes shorter than the stencil reach)
 //   PULL = false: the stored populations of each cell
-// fields[k][cell], k = n, eps, U0, U1, U2, U3; partial[block][5] = block sums of
+// out.f[k][cell], k = n, eps, U0, U1, U2, U3; partial[block][5] = block sums of
 // N^0, T^00, T^0x, T^0y, T^0z, reduced by warp shuffles in a fixed order.
 // ---------------------------------------------------------------------------------------------
 template <class L, class S, bool PULL, bool GENERAL>
 __global__ void __launch_bounds__(kMomThreads) k_fields(const typename S::T* __restrict__ src,
                                                         const __grid_constant__ StepParams p,
-                                                        double* __restrict__ fields,
+                                                        const FieldOut out,
                                                         double* __restrict__ partial,
                                                         int* __restrict__ status, int block0) {
   // blocks [block0, block0 + gridDim.x) of the lattice's kMomThreads-cell blocks (a launch may cover
@@ -1172,12 +1172,12 @@ __global__ void __launch_bounds__(kMomThreads) k_fields(const typename S::T* __r
   }
   if (valid) {
     const double nan = __longlong_as_double(0x7ff8000000000000ll);
-    fields[0 * (long long)p.cells + cl.c] = lw.ok ? lw.n : nan;
-    fields[1 * (long long)p.cells + cl.c] = lw.ok ? lw.eps : nan;
-    fields[2 * (long long)p.cells + cl.c] = lw.ok ? lw.U0 : nan;
-    fields[3 * (long long)p.cells + cl.c] = lw.ok ? lw.Ux : nan;
-    fields[4 * (long long)p.cells + cl.c] = lw.ok ? lw.Uy : nan;
-    fields[5 * (long long)p.cells + cl.c] = lw.ok ? lw.Uz : nan;
+    out.f[0][cl.c] = lw.ok ? lw.n : nan;
+    out.f[1][cl.c] = lw.ok ? lw.eps : nan;
+    out.f[2][cl.c] = lw.ok ? lw.U0 : nan;
+    out.f[3][cl.c] = lw.ok ? lw.Ux : nan;
+    out.f[4][cl.c] = lw.ok ? lw.Uy : nan;
+    out.f[5][cl.c] = lw.ok ? lw.Uz : nan;
     // non-finite populations show as non-finite moments; any other cell without a frame is a
     // Landau failure
     const bool finite = isfinite(m.N0) && isfinite(m.Nx) && isfinite(m.Ny) && isfinite(m.Nz) && isfinite(m.T00) &&

@@ -14,8 +14,8 @@ struct Launchers {
   cudaError_t (*step)(const void* src, void* dst, const StepParams& p, int* status, bool general, int variant,
                       cudaStream_t s);
   // fields and partial sums of the lattice's kMomThreads-cell blocks [block0, block1)
-  cudaError_t (*fields)(const void* src, const StepParams& p, double* fields, double* partial, int* status, bool pull,
-                        int block0, int block1, cudaStream_t s);
+  cudaError_t (*fields)(const void* src, const StepParams& p, const FieldOut& out, double* partial, int* status,
+                        bool pull, int block0, int block1, cudaStream_t s);
   // initial populations of cells [c0, c1)
   cudaError_t (*init)(const double* n, const double* T, const double* u, void* dst, const StepParams& p, int* status,
                       int c0, int c1, cudaStream_t s);
