@@ -144,6 +144,49 @@ __device__ __forceinline__ int src_coord(int x, int n, int bc) {
   }
 }
 
+// src_coord with the shift v known only at run time (one conditional wrap: n >= |v|).
+__device__ __forceinline__ int src_coord_rt(int x, int v, int n, int bc) {
+  const int s = x - v;
+  if ((unsigned)s < (unsigned)n) return s;
+  if (bc) return s < 0 ? 0 : n - 1;
+  return s < 0 ? s + n : s - n;
+}
+
+// The populations' velocities as a table in constant memory, for loops over the populations with
+// a run-time index.
+template <class L>
+struct VelTab {
+  signed char v[L::Q][3];
+};
+template <class L>
+constexpr VelTab<L> make_vel_tab() {
+  VelTab<L> t{};
+  for (int i = 0; i < L::Q; ++i) {
+    t.v[i][0] = (signed char)L::VX[i];
+    t.v[i][1] = (signed char)L::VY[i];
+    t.v[i][2] = (signed char)L::VZ[i];
+  }
+  return t;
+}
+template <class L>
+__constant__ VelTab<L> kVelTab = make_vel_tab<L>();
+
+// Pull offsets of one shell row (fixed y, z): for every population the constant offset plus the
+// row's y and z wrap (or clamp) shifts, worked out once per row by the warp's 32 lanes (four
+// populations each) into roff[Q]; the warp's cells then add only their x shift.  Lattices with
+// bounce-back walls take shell_row_offset per population instead.
+template <class L>
+__device__ __forceinline__ void shell_row_table(long long* roff, const Cell& cl, const StepParams& p) {
+  for (int i = threadIdx.x & 31; i < L::Q; i += 32) {
+    const int vy = kVelTab<L>.v[i][1], vz = kVelTab<L>.v[i][2];
+    long long o = p.off[i];
+    o += (long long)(src_coord_rt(cl.y, vy, p.ny, p.bc[1]) - (cl.y - vy)) * p.nx;
+    o += (long long)(src_coord_rt(cl.z, vz, p.nz, p.bc[2]) - (cl.z - vz)) * p.nxy;
+    roff[i] = o;
+  }
+  __syncwarp();
+}
+
 // True if the pull source of population I lies beyond a bounce-back wall (then the cell takes its
 // own population of the reversed momentum, I ^ 1: mirror pairs are adjacent).
 template <class L, int I>
@@ -773,21 +816,24 @@ struct StepShape {
 // kernel's warps lie in boundary rows, whose y and z shifts are the same for the whole warp; the
 // per-cell shell kernel (lattices shorter than the stencil reach) wraps every coordinate of every
 // cell.
-enum PullPath : int { kPathRow = 1, kPathEdge = 2, kPathShellRow = 3 };
+enum PullPath : int { kPathRow = 1, kPathEdge = 2, kPathShellRow = 3, kPathShellTab = 4 };
 
 // One cell's time step (pull, moments, Landau matching, equilibrium, collision, store).  Invalid
 // lanes (valid = false) carry a clamped in-range cell, compute and store nothing.
 template <class L, class S, bool GENERAL, int VARIANT, int PATH, bool WALLS>
 __device__ __forceinline__ void step_cell(const typename S::T* __restrict__ src, typename S::T* __restrict__ dst,
                                           const StepParams& p, int* __restrict__ status, const Cell cl,
-                                          const bool valid, const bool row_fast = false) {
+                                          const bool valid, const bool row_fast = false,
+                                          const long long* __restrict__ roff = nullptr) {
   using A = typename S::A;
   using ST = typename S::T;
   constexpr bool PACKED = (VARIANT & 1) && std::is_same<A, float>::value;
   constexpr bool KEEP = StepShape<S, VARIANT>::kKeep;
   // Warp-uniform choice: a row warp whose segment is interior pulls with constant offsets; other
   // row warps wrap x only; shell cells resolve wrap / copy-out / bounce-back per population.
-  static_assert(PATH == kPathRow || PATH == kPathEdge || PATH == kPathShellRow, "pull path");
+  static_assert(PATH == kPathRow || PATH == kPathEdge || PATH == kPathShellRow || PATH == kPathShellTab,
+                "pull path");
+  static_assert(PATH != kPathShellTab || !WALLS, "the shell-row table has no bounce-back walls");
   const bool fast = PATH == kPathRow && row_fast;
   const ST* __restrict__ base = src + cl.c;
   ST* __restrict__ out = dst + cl.c;
@@ -805,6 +851,14 @@ __device__ __forceinline__ void step_cell(const typename S::T* __restrict__ src,
     if (fast) return ld(I, base + p.off[i]);
     if constexpr (PATH == kPathRow) return ld(I, base + x_row_offset<L, i, WALLS>(cl, p));
     else if constexpr (PATH == kPathShellRow) return ld(I, base + shell_row_offset<L, i, WALLS>(cl, p, row_fast));
+    else if constexpr (PATH == kPathShellTab) {
+      constexpr int vx = L::VX[i];
+      long long o = roff[i];
+      if constexpr (vx != 0) {
+        if (!row_fast) o += src_coord<vx, false>(cl.x, p.nx, p.bc[0]) - (cl.x - vx);
+      }
+      return ld(I, base + o);
+    }
     else return ld(I, src + pull_index<L, i, GENERAL, WALLS>(cl, p));
   };
   auto store = [&](auto I, A v) {
@@ -893,7 +947,13 @@ __global__ void __launch_bounds__(32, 4 * StepShape<S, VARIANT>::kMinBlocks)
   cl.x = valid ? x : p.nx - 1;
   cl.c = (cl.z * p.ny + cl.y) * p.nx + cl.x;
   const bool xfast = x0 >= p.ix0 && min(x0 + 31, p.nx - 1) < p.ix0 + p.ixn;
-  step_cell<L, S, false, VARIANT, kPathShellRow, WALLS>(src, dst, p, status, cl, valid, xfast);
+  if constexpr (WALLS) {
+    step_cell<L, S, false, VARIANT, kPathShellRow, WALLS>(src, dst, p, status, cl, valid, xfast);
+  } else {
+    __shared__ long long roff[L::Q];
+    shell_row_table<L>(roff, cl, p);
+    step_cell<L, S, false, VARIANT, kPathShellTab, false>(src, dst, p, status, cl, valid, xfast, roff);
+  }
 }
 
 // Shell cells (rows whose y or z lies outside the interior box): z-boundary planes, then the
@@ -948,6 +1008,7 @@ __global__ void __launch_bounds__(kStepThreads, StepShape<S, VARIANT>::kMinBlock
   using ST = typename S::T;
   __shared__ StepParams sp;
   __shared__ int s_tile, s_member;
+  __shared__ long long s_roff[kStepThreads / 32][L::Q];  // shell tiles: each warp's row offsets
   int held = -1;  // member whose parameters sp holds (block-uniform)
   for (;;) {
     if (threadIdx.x == 0) {
@@ -998,7 +1059,13 @@ __global__ void __launch_bounds__(kStepThreads, StepShape<S, VARIANT>::kMinBlock
           cl.x = valid ? x : sp.nx - 1;
           cl.c = (cl.z * sp.ny + cl.y) * sp.nx + cl.x;
           const bool xfast = x0 >= sp.ix0 && min(x0 + 31, sp.nx - 1) < sp.ix0 + sp.ixn;
-          step_cell<L, S, false, VARIANT, kPathShellRow, WALLS>(sb, db, sp, m.status, cl, valid, xfast);
+          if (WALLS && sp.has_wall) {
+            step_cell<L, S, false, VARIANT, kPathShellRow, WALLS>(sb, db, sp, m.status, cl, valid, xfast);
+          } else {
+            long long* roff = s_roff[threadIdx.x >> 5];
+            shell_row_table<L>(roff, cl, sp);
+            step_cell<L, S, false, VARIANT, kPathShellTab, false>(sb, db, sp, m.status, cl, valid, xfast, roff);
+          }
         }
       }
     }
