@@ -121,3 +121,40 @@ def test_reduced_precision_over_1000_steps(storage, tol):
     eu = np.max(np.abs(ugot - uref)) / max(np.max(np.abs(uref)), 0.01)
     print("%s vs f64 after 1000 steps at 64^3: n %.2e eps %.2e u %.2e" % (storage, en, ee, eu))
     assert max(en, ee, eu) < tol
+
+
+# (kind, shape (nz, ny, nx), bc, eta/s, steps): the workload kinds of the benchmark configurations
+# at their step counts, each on a lattice that carries the same fields (the shear wave depends on
+# x only, so 4 x 4 rows of 128 cells stand for the 128^3 cube)
+F16_CASES = [("tube", (800, 1, 1), (0, 0, 1), 0.1, 500), ("shear", (4, 4, 128), (0, 0, 0), 0.1, 2000),
+             ("random", (64, 64, 64), (0, 0, 0), 0.1, 100)]
+
+
+@pytest.mark.parametrize("case", range(len(F16_CASES)))
+def test_f16dev_error_per_config(case):
+    """Half-deviation storage against double storage (which equals the FP64 oracle within 1e-12 per
+    population, test_gpu_parity) on the shock tube, the shear wave and the random field: the field
+    errors are printed (the values quoted for each configuration) and stay bounded; they are above
+    the 1e-5 bar of the float paths (about 11 significant bits per stored deviation)."""
+    kind, shape, bc, eta, steps = F16_CASES[case]
+    if kind == "tube":
+        fields = gen.riemann_tube(shape[0])
+    elif kind == "shear":
+        fields = gen.shear_wave(shape[2], amp=0.05, ny=shape[1], nz=shape[0])
+    else:
+        fields = gen.smooth_random_fields(shape, seed=5, vmax=0.6, sigma_lnT=0.2, density="uniform")
+    res = {}
+    for st in ("f64", "f16dev"):
+        with RLB(shape, order=3, bc=bc, storage=st, eta_over_s=eta) as g:
+            g.init(*fields)
+            g.step(steps)
+            res[st] = g.moments()
+    ref, got = res["f64"], res["f16dev"]
+    en = np.max(np.abs(got["n"] - ref["n"]) / np.abs(ref["n"]))
+    ee = np.max(np.abs(got["eps"] - ref["eps"]) / np.abs(ref["eps"]))
+    uref = ref["U"][1:] / ref["U"][0]
+    ugot = got["U"][1:] / got["U"][0]
+    eu = np.max(np.abs(ugot - uref)) / max(np.max(np.abs(uref)), 0.01)
+    print("f16dev %s %s, %d steps, eta/s %.2f: n %.2e eps %.2e u %.2e" % (kind, shape, steps, eta, en, ee, eu))
+    assert np.isfinite([en, ee, eu]).all()
+    assert max(en, ee, eu) < 0.1
