@@ -178,6 +178,8 @@ rlb_status rlb_set_populations(rlb_ctx* ctx, const double* f, int on_device);
  *   15..18 row segments (15, 17) and row tiles (16, 18) in three consumer groups of four warps
  *         per block, 4 (15, 16) or 2 (17, 18) producer warps; float storage relaxes each cell in
  *         one warp here instead of two.
+ *   19    96-cell row tiles (rows of at most 96 cells; 96, 48 and 32 fill them), four consumer
+ *         groups of three warps, one warp per float cell.
  * Each variant repeats one step from the current populations into the spare buffer `reps` times, so
  * the state does not change; this is allowed only before the first step after rlb_init /
  * rlb_set_populations (RLB_ESTATE otherwise).  *variant (may be NULL) receives the choice;

@@ -24,8 +24,8 @@ NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-
 INSTANCES = [(o, s) for o in (3, 2) for s in (0, 1, 2)]
 # step-kernel variants compiled per (order, storage): one for double storage, four for float ones
 VARIANT_UNITS = [(o, s, v) for o, s in INSTANCES for v in ((0,) if s == 0 else (0, 1, 2, 3))]
-# pipelined step kernel per (order, storage), tile width and tile kind (row tiles: width 128 only)
-PIPE_UNITS = [(o, s, tx, rows) for o, s in INSTANCES for tx, rows in ((64, 0), (128, 0), (128, 1))]
+# pipelined step kernel per (order, storage), tile width and tile kind (row tiles: widths 128 and 96)
+PIPE_UNITS = [(o, s, tx, rows) for o, s in INSTANCES for tx, rows in ((64, 0), (128, 0), (128, 1), (96, 1))]
 
 
 def _nvcc():

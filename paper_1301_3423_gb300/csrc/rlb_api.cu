@@ -188,12 +188,12 @@ static bool variant_available(const rlb_ctx* c, int v) {
 
 // The variant rlb_step uses unless asked otherwise: the first one that suits the context in an
 // order measured on GB300 (32^3 to 256^3 lattices, third order): for float storage one warp per
-// cell in row tiles, then in row segments (0.83 of the copy bandwidth at 256^3), then the two-warp
-// shapes; for half storage row tiles first (whose 128-cell rows step 1.26x faster in row tiles),
+// cell in 96-cell row tiles where the rows fill them exactly, then in 128-cell row tiles, then in
+// row segments (0.83 of the copy bandwidth at 256^3), then the two-warp shapes; for half storage row tiles first (whose 128-cell rows step 1.26x faster in row tiles),
 // then row segments in three consumer groups; then the register kernels; the register kernel for double storage (whose step is bound by the
 // double-precision pipe, which the register kernel's 4 warps per scheduler keep busier).
 static int default_variant(const rlb_ctx* c) {
-  static const int pref_f32[] = {16, 15, 18, 17, 5, 12, 4, 13, 8, 6, 9, 7, 3};
+  static const int pref_f32[] = {19, 16, 15, 18, 17, 5, 12, 4, 13, 8, 6, 9, 7, 3};
   static const int pref_f16[] = {12, 16, 15, 13, 4, 8, 6, 5, 9, 7, 2};
   const int* pref = c->prm.storage == RLB_F32 ? pref_f32 : pref_f16;
   const int n = c->prm.storage == RLB_F32 ? (int)(sizeof(pref_f32) / sizeof(int)) : (int)(sizeof(pref_f16) / sizeof(int));
@@ -207,9 +207,11 @@ static int default_variant(const rlb_ctx* c) {
         if (!pipe_layout(pref[k], c->q, (int)c->elem, c->smem_per_sm, c->smem_optin, &lay)) continue;
         const int elem = (int)c->elem;
         const bool one = elem == 4 && !lay.split;  // one warp per float cell
-        const bool fits = lay.rows ? (one ? rows_fit(c->sp.nx, lay.tx, elem, c->sp.bc[0], vmax_x(c))
-                                          : rows_fit_solo(c->sp.nx, lay.tx, elem, c->sp.bc[0], vmax_x(c)))
-                                   : pipe_fits(c->sp.nx, lay.tx, elem, fill_eighths(lay, elem));
+        bool fits = lay.rows ? (one ? rows_fit(c->sp.nx, lay.tx, elem, c->sp.bc[0], vmax_x(c))
+                                    : rows_fit_solo(c->sp.nx, lay.tx, elem, c->sp.bc[0], vmax_x(c)))
+                             : pipe_fits(c->sp.nx, lay.tx, elem, fill_eighths(lay, elem));
+        // 96-cell row tiles only where the rows fill them exactly (96-, 48- and 32-cell rows)
+        if (lay.tx == 96) fits = fits && (96 / c->sp.nx) * c->sp.nx == 96;
         if (!fits) continue;
       }
       if (variant_available(c, pref[k])) return pref[k];

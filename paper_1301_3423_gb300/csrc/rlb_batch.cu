@@ -27,7 +27,7 @@ struct GraphCache {
   cudaGraphExec_t exec = nullptr;
   long nsteps = 0, version = -1;
   int variant = -1, nmembers = 0, tiles = 0, row_tiles = -1, walls = -1, pipe_tiles = -1, pipe_walls = -1,
-      rtile_tiles = -1;
+      rtile_tiles = -1, r96_tiles = -1;
 };
 
 }  // namespace
@@ -55,6 +55,11 @@ struct rlb_batch {
   int* d_rtile_tm = nullptr;     // member index of every row tile (pipelined kernel with row tiles)
   int rtile_tm_capacity = 0;
   int rtile_tiles = 0;
+  PipeLayout lay96{};            // 96-cell row tiles beside a 128-cell row-tile variant (tx 0: none)
+  int v96 = -1;                  // their variant
+  int* d_r96_tm = nullptr;       // member index of every 96-cell row tile
+  int r96_tm_capacity = 0;
+  int r96_tiles = 0;
   int* pipe_timeout = nullptr;   // status word that counts the pipelined kernel's expired waits
   PipeLayout lay{};              // block layout of the current pipelined variant
   int sms = 0, smem_per_sm = 0, smem_optin = 0;
@@ -117,18 +122,41 @@ static bool variant_exists(const rlb_batch* b, int v, PipeLayout* lay = nullptr)
   return pipe_layout(v, q, elem_of(b->storage), b->smem_per_sm, b->smem_optin, lay);
 }
 
-// How a member runs under step variant v: 2 row tiles, 1 row segments (pipelined kernel), 0 the
-// register kernels (variant v itself, or reg_fallback for a pipelined v).  Rows that fill segment
-// tiles go to row tiles too, except with two warps per float cell (measured on GB300 at 128^3:
-// one warp per float cell 1.13x faster in row tiles, half storage 1.26x; two warps per float cell
-// 1.04x faster in segments).
-static int member_mode(const rlb_batch* b, const StepParams& p, int v, const PipeLayout& lay) {
+// Lanes of a row tile of tx cells that hold cells (0 if the rows do not fit).
+static int row_tile_fill(int nx, int tx) { return nx <= tx ? (tx / nx) * nx : 0; }
+
+// How a member runs under step variant v: 3 the 96-cell row tiles beside a 128-cell row-tile
+// variant, 2 the variant's row tiles, 1 row segments (pipelined kernel), 0 the register kernels
+// (variant v itself, or reg_fallback for a pipelined v).  A member takes the row tiles whose lanes
+// it fills the larger share of (96-cell rows: all of a 96-cell tile against 3/4 of a 128-cell one).
+// Rows that fill segment tiles go to row tiles too, except with two warps per float cell (measured
+// on GB300 at 128^3: one warp per float cell 1.13x faster in row tiles, half storage 1.26x; two
+// warps per float cell 1.04x faster in segments).  96-cell tiles exist as row tiles only.
+static int member_mode(const rlb_batch* b, const StepParams& p, int v, const PipeLayout& lay, const PipeLayout& lay96) {
   if (v < kNumRegVariants) return 0;
   const int vmax = b->order == 3 ? Quad3::VMAX_X : Quad2::VMAX_X;
   const int elem = elem_of(b->storage);
-  const bool seg = pipe_fits(p.nx, lay.tx, elem, fill_eighths(lay, elem));
-  if (lay.rows && rows_fit(p.nx, lay.tx, elem, p.bc[0], vmax) && (!seg || !lay.split)) return 2;
+  const bool seg = lay.tx != 96 && pipe_fits(p.nx, lay.tx, elem, fill_eighths(lay, elem));
+  const bool rows = lay.rows && rows_fit(p.nx, lay.tx, elem, p.bc[0], vmax);
+  if (lay96.tx == 96 && rows_fit(p.nx, 96, elem, p.bc[0], vmax) &&
+      (!rows || row_tile_fill(p.nx, 96) * lay.tx > row_tile_fill(p.nx, lay.tx) * 96))
+    return 3;
+  if (rows && (!seg || !lay.split)) return 2;
   return seg ? 1 : 0;
+}
+
+// The 96-cell row-tile variant with the warps of 128-cell row-tile variant v (-1 if none).
+static int rows96_sibling(int v) {
+  if (v < kNumRegVariants || v >= kNumVariantsTotal) return -1;
+  const PipeConfig& c = kPipeConfigs[v - kNumRegVariants];
+  if (!c.rows || c.tx != 128) return -1;
+  for (int k = 0; k < kNumPipeConfigs; ++k) {
+    const PipeConfig& d = kPipeConfigs[k];
+    if (d.rows && d.tx == 96 && d.cons_warps == c.cons_warps && d.producers == c.producers &&
+        d.ctas_per_sm == c.ctas_per_sm && d.split == c.split)
+      return kNumRegVariants + k;
+  }
+  return -1;
 }
 
 // The row-segment variant with the block layout of row-tile variant v (the shape the batch runs its
@@ -144,6 +172,18 @@ static int segment_sibling(int v) {
       return kNumRegVariants + k;
   }
   return -1;
+}
+
+// The 96-cell companion of variant v for this batch's storage: its variant (-1 if none) and
+// layout in *lay96 (tx 0 if none).
+static int companion96(const rlb_batch* b, int v, PipeLayout* lay96) {
+  *lay96 = PipeLayout{};
+  const int v96 = rows96_sibling(v);
+  if (v96 < 0 || !variant_exists(b, v96, lay96)) {
+    *lay96 = PipeLayout{};
+    return -1;
+  }
+  return v96;
 }
 
 // Grow a device tile table to hold n entries and upload `tm` into it.
@@ -213,6 +253,9 @@ static rlb_status upload_table(rlb_batch* b, long nsteps, int variant, int* nmem
   b->pipe_timeout = nullptr;
   const bool pipe = variant >= kNumRegVariants && variant_exists(b, variant, &b->lay);
   if (!pipe) b->lay = PipeLayout{};
+  b->v96 = pipe ? companion96(b, variant, &b->lay96) : -1;
+  if (!pipe) b->lay96 = PipeLayout{};
+  std::vector<int> r96_tm;
   for (const Member& m : b->members) {
     if (!m.ctx || m.steps_left <= 0) continue;
     BatchMember d{};
@@ -222,12 +265,12 @@ static rlb_status upload_table(rlb_batch* b, long nsteps, int variant, int* nmem
     d.status = m.ctx->status;
     d.parity0 = m.ctx->cur;
     d.steps_left = (int)std::min<long>(m.steps_left, nsteps);
-    const int mode = member_mode(b, d.p, pipe ? variant : 0, b->lay);
+    const int mode = member_mode(b, d.p, pipe ? variant : 0, b->lay, b->lay96);
     if (mode > 0) {
       // pipelined: ceil(nx / TX) segment tiles per row, or groups of TX / nx rows
-      std::vector<int>& tm = mode == 2 ? rtile_tm : pipe_tm;
+      std::vector<int>& tm = mode == 3 ? r96_tm : (mode == 2 ? rtile_tm : pipe_tm);
       d.pipe_tile_begin = (int)tm.size();
-      const long long nt = pipe_tile_count(d.p.nx, d.p.ny, d.p.nz, b->lay.tx, mode == 2);
+      const long long nt = pipe_tile_count(d.p.nx, d.p.ny, d.p.nz, mode == 3 ? 96 : b->lay.tx, mode >= 2);
       if ((long long)tm.size() + nt > 0x7fffffffll) return bfail(b, RLB_EINVAL, "too many tiles in one batch");
       tm.resize(tm.size() + nt, (int)t.size());
       if (d.p.has_wall) b->pipe_walls = 1;
@@ -250,16 +293,19 @@ static rlb_status upload_table(rlb_batch* b, long nsteps, int variant, int* nmem
   b->shell_tiles = (int)shell_tm.size();
   b->pipe_tiles = (int)pipe_tm.size();
   b->rtile_tiles = (int)rtile_tm.size();
+  b->r96_tiles = (int)r96_tm.size();
   for (BatchMember& d : t) d.shell_tile_begin += b->row_tiles;
   std::vector<int> tm(row_tm);
   tm.insert(tm.end(), shell_tm.begin(), shell_tm.end());
   const int tiles = (int)tm.size();
   *nmembers = (int)t.size();
-  *total_tiles = tiles + b->pipe_tiles + b->rtile_tiles;
+  *total_tiles = tiles + b->pipe_tiles + b->rtile_tiles + b->r96_tiles;
   if (t.empty()) return RLB_OK;
   rlb_status st = upload_tiles(b, &b->d_pipe_tm, &b->pipe_tm_capacity, pipe_tm, "pipelined tile table");
   if (st != RLB_OK) return st;
   st = upload_tiles(b, &b->d_rtile_tm, &b->rtile_tm_capacity, rtile_tm, "row-tile table");
+  if (st != RLB_OK) return st;
+  st = upload_tiles(b, &b->d_r96_tm, &b->r96_tm_capacity, r96_tm, "96-cell row-tile table");
   if (st != RLB_OK) return st;
   if ((int)t.size() > b->d_capacity) {
     if (b->d_members) cudaFree(b->d_members);
@@ -314,14 +360,16 @@ static int grid_of(rlb_batch* b, int variant) { return b->sms * b->launch->batch
 // the register kernels (row tiles, shell tiles) over the other members' tiles.
 static rlb_status enqueue_step(rlb_batch* b, int k, int variant, int* counters) {
   cudaError_t e = cudaSuccess;
-  for (int rows = 0; rows < 2; ++rows) {
-    const int ntiles = rows ? b->rtile_tiles : b->pipe_tiles;
+  // row segments, 128-cell row tiles, 96-cell row tiles
+  for (int kind = 0; kind < 3; ++kind) {
+    const int ntiles = kind == 0 ? b->pipe_tiles : (kind == 1 ? b->rtile_tiles : b->r96_tiles);
     if (ntiles == 0) continue;
-    const PipeParams pp{b->lay.producers, ntiles, b->lay.nstage, b->lay.groups};
-    const int grid = std::min(b->sms * b->lay.ctas_per_sm, ntiles);
-    e = b->launch->pipe_batch_step(b->d_members, rows ? b->d_rtile_tm : b->d_pipe_tm, k, pp, b->pipe_timeout,
-                                   b->lay.tx, rows, b->lay.split, b->pipe_walls, grid, b->lay.threads, b->lay.smem,
-                                   b->stream);
+    const PipeLayout& lay = kind == 2 ? b->lay96 : b->lay;
+    const int* tm = kind == 0 ? b->d_pipe_tm : (kind == 1 ? b->d_rtile_tm : b->d_r96_tm);
+    const PipeParams pp{lay.producers, ntiles, lay.nstage, lay.groups};
+    const int grid = std::min(b->sms * lay.ctas_per_sm, ntiles);
+    e = b->launch->pipe_batch_step(b->d_members, tm, k, pp, b->pipe_timeout, lay.tx, kind > 0, lay.split,
+                                   b->pipe_walls, grid, lay.threads, lay.smem, b->stream);
     ++b->launches;
     if (e != cudaSuccess) return bfail(b, RLB_ECUDA, std::string("batched pipelined step: ") + cudaGetErrorString(e));
   }
@@ -368,7 +416,8 @@ extern "C" rlb_status rlb_batch_run(rlb_batch* b, long nsteps, int use_graph, in
       GraphCache& gc = b->graph;
       if (!gc.exec || gc.nsteps != nsteps || gc.version != b->version || gc.variant != b->variant ||
           gc.nmembers != nmem || gc.tiles != tiles || gc.row_tiles != b->row_tiles || gc.walls != b->walls ||
-          gc.pipe_tiles != b->pipe_tiles || gc.pipe_walls != b->pipe_walls || gc.rtile_tiles != b->rtile_tiles) {
+          gc.pipe_tiles != b->pipe_tiles || gc.pipe_walls != b->pipe_walls || gc.rtile_tiles != b->rtile_tiles ||
+          gc.r96_tiles != b->r96_tiles) {
         if (b->graph.exec) cudaGraphExecDestroy(b->graph.exec);
         b->graph.exec = nullptr;
         cudaStream_t cs;
@@ -401,9 +450,11 @@ extern "C" rlb_status rlb_batch_run(rlb_batch* b, long nsteps, int use_graph, in
         gc.pipe_tiles = b->pipe_tiles;
         gc.pipe_walls = b->pipe_walls;
         gc.rtile_tiles = b->rtile_tiles;
+        gc.r96_tiles = b->r96_tiles;
       }
       BATCH_CUDA(b, cudaGraphLaunch(b->graph.exec, b->stream));
-      b->launches += nsteps * ((b->row_tiles > 0) + (b->shell_tiles > 0) + (b->pipe_tiles > 0) + (b->rtile_tiles > 0));
+      b->launches += nsteps * ((b->row_tiles > 0) + (b->shell_tiles > 0) + (b->pipe_tiles > 0) + (b->rtile_tiles > 0) +
+                               (b->r96_tiles > 0));
     } else {
       rlb_status st = enqueue_run(b, nsteps, nmem, tiles, b->variant);
       if (st != RLB_OK) return st;
@@ -484,7 +535,10 @@ extern "C" int rlb_batch_member_variant(const rlb_batch* b, int slot) {
   if (b->variant < kNumRegVariants) return b->variant;
   PipeLayout lay;
   if (!variant_exists(b, b->variant, &lay)) return reg_fallback(b);
-  const int mode = member_mode(b, b->members[slot].ctx->sp, b->variant, lay);
+  PipeLayout lay96;
+  const int v96 = companion96(b, b->variant, &lay96);
+  const int mode = member_mode(b, b->members[slot].ctx->sp, b->variant, lay, lay96);
+  if (mode == 3) return v96;
   if (mode == 2) return b->variant;
   if (mode == 1) return segment_sibling(b->variant);
   return reg_fallback(b);
@@ -502,6 +556,7 @@ extern "C" rlb_status rlb_batch_destroy(rlb_batch* b) {
   if (b->d_tile_member) cudaFree(b->d_tile_member);
   if (b->d_pipe_tm) cudaFree(b->d_pipe_tm);
   if (b->d_rtile_tm) cudaFree(b->d_rtile_tm);
+  if (b->d_r96_tm) cudaFree(b->d_r96_tm);
   if (b->d_counters) cudaFree(b->d_counters);
   delete b;
   return RLB_OK;

@@ -14,7 +14,7 @@ constexpr int kDefaultStepVariant = 0;  // step-kernel variant before autotuning
 // rows start on 16-byte boundaries.
 constexpr int kNumRegVariants = 4;
 struct PipeConfig {
-  int tx;           // tile width in cells (64 or 128)
+  int tx;           // tile width in cells (64 or 128; 96 for row tiles)
   int cons_warps;   // consumer warps per block: TX / 32 per tile, twice that with float storage
                     // (two warps per cell); a multiple of the warps per tile
   int ctas_per_sm;  // resident blocks per SM (the shared memory is split between them)
@@ -32,7 +32,7 @@ constexpr PipeConfig kPipeConfigs[] = {
     {128, 8, 1, 8, 0, 1}, {128, 8, 1, 4, 0, 1},  {64, 8, 1, 8, 0, 1},  {64, 4, 1, 4, 0, 1},
     {128, 8, 1, 6, 0, 1}, {64, 8, 1, 4, 0, 1},   {128, 4, 1, 4, 0, 1}, {64, 2, 1, 4, 0, 1},
     {128, 8, 1, 4, 1, 1}, {128, 8, 1, 8, 1, 1},  {128, 4, 1, 4, 1, 1}, {128, 12, 1, 4, 0, 0},
-    {128, 12, 1, 4, 1, 0}, {128, 12, 1, 2, 0, 0}, {128, 12, 1, 2, 1, 0}};
+    {128, 12, 1, 4, 1, 0}, {128, 12, 1, 2, 0, 0}, {128, 12, 1, 2, 1, 0}, {96, 12, 1, 4, 1, 0}};
 constexpr int kNumPipeConfigs = sizeof(kPipeConfigs) / sizeof(kPipeConfigs[0]);
 constexpr int kNumVariantsTotal = kNumRegVariants + kNumPipeConfigs;
 constexpr int kPipeMaxStages = 16;

@@ -78,6 +78,7 @@ cudaError_t convert_pops(void* pop, double* dbl, int i0, int i1, bool to_f64, co
 cudaError_t pipe_step(const void* src, void* dst, const StepParams& p, const PipeParams& pp, int* status, int tx,
                       int rows, int split, int grid, int threads, int smem, cudaStream_t s) {
   if (rows) {
+    if (tx == 96) return RLB_RFN(pipe, 96)(src, dst, p, pp, status, split, grid, threads, smem, s);
     if (tx != 128) return cudaErrorInvalidValue;
     return RLB_RFN(pipe, 128)(src, dst, p, pp, status, split, grid, threads, smem, s);
   }
@@ -88,6 +89,7 @@ cudaError_t pipe_step(const void* src, void* dst, const StepParams& p, const Pip
 cudaError_t pipe_batch_step(const BatchMember* m, const int* tm, int launch, const PipeParams& pp, int* timeout, int tx,
                             int rows, int split, int walls, int grid, int threads, int smem, cudaStream_t s) {
   if (rows) {
+    if (tx == 96) return RLB_RFN(pipe_batch, 96)(m, tm, launch, pp, timeout, split, walls, grid, threads, smem, s);
     if (tx != 128) return cudaErrorInvalidValue;
     return RLB_RFN(pipe_batch, 128)(m, tm, launch, pp, timeout, split, walls, grid, threads, smem, s);
   }

@@ -54,8 +54,8 @@ cudaError_t launch_pipe_batch(const BatchMember* m, const int* tm, int launch, c
   return cudaGetLastError();
 }
 
-// One warp per float cell exists for float storage with 128-cell tiles only.
-constexpr bool kOneWarp = std::is_same<S, StoreF32>::value && RLB_INST_TX == 128;
+// One warp per float cell exists for float storage with 128-cell tiles and 96-cell row tiles.
+constexpr bool kOneWarp = std::is_same<S, StoreF32>::value && (RLB_INST_TX == 128 || RLB_INST_TX == 96);
 }  // namespace
 
 // One time step of every active batch member on the pipelined kernel (walls: some member has

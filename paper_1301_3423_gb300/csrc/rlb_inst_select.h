@@ -53,13 +53,17 @@ constexpr int kVariants = kFloat ? kNumVariants : 1;
 RLB_DECLARE_PIPE(64)
 RLB_DECLARE_PIPE(128)
 #undef RLB_DECLARE_PIPE
-// ... and with row tiles (RLB_INST_ROWS = 1), tile width 128 only.
+// ... and with row tiles (RLB_INST_ROWS = 1), tile widths 128 and 96.
 #define RLB_RFN(fn, tx) RLB_CAT7(fn, _o, RLB_INST_ORDER, _s, RLB_INST_STORAGE, _r, tx)
-cudaError_t RLB_RFN(pipe, 128)(const void* src, void* dst, const StepParams& p, const PipeParams& pp, int* status,
-                               int split, int grid, int threads, int smem, cudaStream_t s);
-cudaError_t RLB_RFN(pipe_batch, 128)(const BatchMember* m, const int* tm, int launch, const PipeParams& pp,
-                                     int* timeout, int split, int walls, int grid, int threads, int smem,
-                                     cudaStream_t s);
+#define RLB_DECLARE_ROWS(tx)                                                                                   \
+  cudaError_t RLB_RFN(pipe, tx)(const void* src, void* dst, const StepParams& p, const PipeParams& pp, int* status, \
+                                int split, int grid, int threads, int smem, cudaStream_t s);                      \
+  cudaError_t RLB_RFN(pipe_batch, tx)(const BatchMember* m, const int* tm, int launch, const PipeParams& pp,        \
+                                      int* timeout, int split, int walls, int grid, int threads, int smem,          \
+                                      cudaStream_t s);
+RLB_DECLARE_ROWS(128)
+RLB_DECLARE_ROWS(96)
+#undef RLB_DECLARE_ROWS
 
 RLB_DECLARE_VARIANT(0)
 RLB_DECLARE_VARIANT(1)

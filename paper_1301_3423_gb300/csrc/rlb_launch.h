@@ -30,7 +30,7 @@ struct Launchers {
   // resident blocks per SM of the batched step for a variant
   int (*batch_blocks_per_sm)(int variant);
   // one time step of the pipelined kernel with tile width tx (64 or 128), row tiles if rows != 0
-  // (tx 128 only), float cells split between two warps if split != 0 (float storage)
+  // (tx 128 or 96), float cells split between two warps if split != 0 (float storage)
   cudaError_t (*pipe_step)(const void* src, void* dst, const StepParams& p, const PipeParams& pp, int* status, int tx,
                            int rows, int split, int grid, int threads, int smem, cudaStream_t s);
   // one time step of the batched pipelined kernel (launch index `launch`) over the members' tiles;

@@ -12,12 +12,13 @@
 // copies cannot express (a copy-out or bounce-back x, the reversed population beyond a y or z
 // wall) is patched in shared memory by the consumer warp before it reads the stage.
 //
-// Consumer warps own one 32-cell part of a tile each and read population i of lane x at the
-// compile-time offset i * BX + r_i + x of the stage (r_i = -vx_i mod the copy granule), twice:
-// once for the moments and once for the collision, whose result goes straight to global memory
-// with one coalesced store per population.  The populations never sit in registers as a whole,
-// so a consumer needs ~100 registers instead of Q + ~40, and the loads that feed a tile are issued
-// by one producer lane per population instead of 32 lanes each computing an address.
+// Consumer warps own one 32-cell part of a tile each (with float storage optionally two warps per
+// part, each taking half the populations) and read population i of lane x at the compile-time
+// offset i * BX + r_i + x of the stage (r_i = -vx_i mod the copy granule), twice: once for the
+// moments and once for the collision, whose result goes straight to global memory with one
+// coalesced store per population.  The populations never sit in registers as a whole, so a
+// consumer needs at most 128 registers instead of Q + ~40, and the loads that feed a tile are
+// issued by one producer lane per population instead of 32 lanes each computing an address.
 //
 // Row tiles (ROWS): on an x-periodic lattice with rows of nx <= TX cells a tile is G = TX / nx
 // consecutive rows (lane q of the tile is cell x = q mod nx of row q / nx).  Population i of those
@@ -32,9 +33,9 @@
 // producer and that group take the stage's uses in order: when either waits for use u of a stage,
 // use u - 1 is complete and use u + 1 cannot be, and the parity of u names the right phase.
 // full[s] completes when every producer has arrived for the stage's tile and its copies have
-// landed; empty[s] when every consumer warp of that tile has finished reading it.  Every wait is bounded
-// (kPipeWaitNs); a wait that runs out counts in status[kStatusTimeout], and the producer then waits
-// (bounded) for the copies it has in flight before it returns.
+// landed; empty[s] when every consumer warp of that tile has finished reading it.  Every wait is
+// bounded (kPipeWaitNs); a wait that runs out counts in status[kStatusTimeout], and the producer
+// then waits (bounded) for the copies it has in flight before it returns.
 #pragma once
 
 #include <stdint.h>

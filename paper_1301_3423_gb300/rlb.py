@@ -21,7 +21,7 @@ VARIANT_NAMES = ["registers/scalar", "registers/paired", "registers(168)/scalar"
                  "pipe tx128 8c8p", "pipe tx128 8c4p", "pipe tx64 8c8p", "pipe tx64 4c4p", "pipe tx128 8c6p",
                  "pipe tx64 8c4p", "pipe tx128 4c4p", "pipe tx64 2c4p", "rows tx128 8c4p", "rows tx128 8c8p",
                  "rows tx128 4c4p", "pipe tx128 12c4p 1w", "rows tx128 12c4p 1w", "pipe tx128 12c2p 1w",
-                 "rows tx128 12c2p 1w"]
+                 "rows tx128 12c2p 1w", "rows tx96 12c4p 1w"]
 BC = {"periodic": 0, "copyout": 1, "bounceback": 2}
 
 

@@ -28,6 +28,10 @@ MEMBERS = [
     ((6, 5, 128), (0, 0, 0), 0.1, 9, "random"),
     ((5, 4, 192), (1, 0, 0), 0.1, 7, "random"),
     ((4, 6, 128), (2, 0, 2), 0.1, 5, "random"),
+    # rows that fill 96-cell row tiles exactly (with a 128-cell row-tile variant they take the
+    # 96-cell companion)
+    ((6, 5, 96), (0, 0, 0), 0.1, 9, "random"),
+    ((5, 6, 48), (0, 2, 2), 0.1, 6, "random"),
 ]
 
 
@@ -52,7 +56,7 @@ def make(order, storage, variant, k, stream=None):
                                                    (3, "f32", 5), (3, "f32", 4), (2, "f32", 5), (3, "f16dev", 4),
                                                    (3, "f64", 11), (3, "f32", 12), (3, "f32", 13), (2, "f32", 12),
                                                    (3, "f16dev", 13), (2, "f64", 14), (3, "f32", 15), (3, "f32", 16),
-                                                   (3, "f16dev", 16), (2, "f32", 18)])
+                                                   (3, "f16dev", 16), (2, "f32", 18), (3, "f32", 19)])
 @pytest.mark.parametrize("graph", [True, False])
 def test_batched_members_equal_solo_runs(order, storage, variant, graph):
     """Variants 0-3: every member on the register kernels.  Variants 4 to 11: members whose rows
@@ -70,9 +74,11 @@ def test_batched_members_equal_solo_runs(order, storage, variant, graph):
         used = [b.member_variant(s) for s in slots]  # the variant each member runs with in the batch
         if variant >= 4:
             assert any(v == variant for v in used) and any(v != variant for v in used)
-        if rlbmod.VARIANT_NAMES[max(variant, 0)].startswith("rows"):
+        if rlbmod.VARIANT_NAMES[max(variant, 0)].startswith("rows tx128"):
             # a row-segment member beside the row-tile ones
             assert any(v >= 4 and rlbmod.VARIANT_NAMES[v].startswith("pipe") for v in used)
+        if variant == 16:
+            assert 19 in used  # the 96-cell companion
         solo = []
         for k in range(len(MEMBERS)):
             ctx, steps = make(order, storage, used[k] if variant >= 0 else variant, k)

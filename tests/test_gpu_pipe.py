@@ -231,13 +231,14 @@ ROW_CASES = [((7, 13, 128), (0, 0, 0)), ((5, 11, 64), (0, 0, 0)), ((6, 9, 40), (
 
 
 @pytest.mark.parametrize("storage,rows,seg", [("f32", 12, 5), ("f32", 13, 4), ("f32", 16, 15), ("f32", 18, 17),
-                                              ("f16dev", 12, 5), ("f16dev", 14, 10), ("f16dev", 16, 15)])
+                                              ("f16dev", 12, 5), ("f16dev", 14, 10), ("f16dev", 16, 15),
+                                              ("f32", 19, 16), ("f16dev", 19, 16)])
 @pytest.mark.parametrize("case", range(len(ROW_CASES)))
 def test_row_tiles_equal_row_segments_bitwise(storage, rows, seg, case):
     """Row tiles pull every cell's populations from the same source cells as row segments of the
     same block layout and evaluate the same arithmetic on them, so after 7 steps the populations
     are bitwise equal (the segment kernel's x wrap is split copies; the row tiles' is a per-lane
-    offset into one copy of the whole rows)."""
+    offset into one copy of the whole rows).  96-cell row tiles (19) against 128-cell ones (16)."""
     shape, bc = ROW_CASES[case]
     n, T, u = gen.smooth_random_fields(shape, seed=40 + case, vmax=0.5, sigma_lnT=0.2)
     out = {}
@@ -309,3 +310,5 @@ def test_row_tiles_default_and_availability():
         assert g.variant == 16  # one warp per cell, row tiles
     with RLB((8, 8, 256), order=3, storage="f32") as g:
         assert g.variant == 15  # one warp per cell, row segments
+    with RLB((8, 8, 96), order=3, storage="f32") as g:
+        assert g.variant == 19  # 96-cell row tiles
