@@ -374,13 +374,14 @@ def run_serving(args, stream):
     """Poisson request stream (mean 20 / s, 40 requests, sides up to 384 drawn with probability
     proportional to 1/L^3, full step counts) plus three 384^3 float shear-wave requests (2000 steps)
     early in the stream, through the continuous-batching server under a 150 GB budget: two 384^3
-    lattices fit (58 GB each), the third waits for memory."""
+    lattices fit (58 GB each), the third waits for memory.  Reduced-precision simulations that
+    break down numerically are rerun in double storage (listed under "escalated")."""
     from paper_1301_3423_gb300 import serve
     reqs = serve.poisson_requests(40, rate=20.0, seed=5, step_scale=args.batch_scale, f16_fraction=0.3)
     for j, t in enumerate((0.0, 0.02, 0.04)):
         reqs.append(serve.Request(1000 + j, "shear", (384, 384, 384), 0.1, max(1, int(round(2000 * args.batch_scale))),
                                   "f32", 77 + j, t))
-    srv = serve.Server(hbm_budget=150e9, chunk=25, stream=stream)
+    srv = serve.Server(hbm_budget=150e9, chunk=25, stream=stream, escalate=True)
     try:
         st = srv.run(reqs, realtime=True, max_wall=900)
     finally:
@@ -390,6 +391,10 @@ def run_serving(args, stream):
     st["not_ok"] = [{"rid": r.rid, "status": r.status, "detail": r.detail[:200], "kind": by_id[r.rid].kind,
                      "shape": list(by_id[r.rid].shape), "eta_over_s": by_id[r.rid].eta_over_s,
                      "storage": by_id[r.rid].storage} for r in srv.results if r.status != "ok"]
+    st["escalated"] = [{"rid": r.rid, "detail": r.detail[:200], "kind": by_id[r.rid].kind,
+                        "shape": list(by_id[r.rid].shape), "eta_over_s": by_id[r.rid].eta_over_s,
+                        "from": by_id[r.rid].storage, "status": r.status}
+                       for r in srv.results if r.storage == "f64" and by_id[r.rid].storage != "f64"]
     st.update({"rate_per_s": 20.0, "step_scale": args.batch_scale,
                "largest_side": max(max(r.shape) if r.kind != "tube" else 0 for r in reqs),
                "f16dev_requests": sum(r.storage == "f16dev" for r in reqs),

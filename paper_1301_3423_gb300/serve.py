@@ -12,7 +12,10 @@ requests are admitted in the next round.
 
 Failures are results, not exceptions: a request larger than the whole budget is rejected, one whose
 context cannot be created (e.g. RLB_ENOMEM) or whose read-back fails is marked failed, and
-cancel(rid) removes a waiting or running request between rounds, releasing its memory.
+cancel(rid) removes a waiting or running request between rounds, releasing its memory.  With
+``escalate`` a float or half-storage simulation that breaks down numerically (cells without a
+Landau frame, non-finite populations) is run again from its initial state in double storage; its
+result says so and keeps the original arrival time, so the rerun counts in its time to solution.
 
 Everything numerical runs in librlb; this module only schedules.
 """
@@ -23,7 +26,7 @@ import numpy as np
 
 from paper_inputs import fields as gen
 
-from .rlb import RLB, Batch, RLBError
+from .rlb import RLB, RLB_ENAN, RLB_ENONCONV, Batch, RLBError
 
 
 @dataclasses.dataclass
@@ -33,10 +36,11 @@ class Request:
     shape: tuple          # (nz, ny, nx)
     eta_over_s: float
     steps: int
-    storage: str          # "f32" or "f16dev"
+    storage: str          # "f32", "f16dev" (or "f64")
     seed: int
     arrival: float        # seconds after the stream starts
     bc: tuple = (0, 0, 0)
+    escalated_from: str = ""  # the storage of a run that broke down, when this is its rerun
 
 
 @dataclasses.dataclass
@@ -53,6 +57,7 @@ class Result:
     steps: int              # steps taken
     status: str = "ok"      # "ok", "rejected", "failed" or "cancelled"
     detail: str = ""
+    storage: str = ""       # the storage precision the result was computed in
 
     @property
     def tts(self):
@@ -104,10 +109,13 @@ class Server:
     default; the host-side tests pass fakes), ``bytes_of`` gives a request's device bytes."""
 
     def __init__(self, order=3, hbm_budget=150e9, chunk=50, use_graph=True, stream=None, autotune=False,
-                 landau_fp64=False, solo_cells=128 ** 3, context=None, batch=None, bytes_of=None):
+                 landau_fp64=False, solo_cells=128 ** 3, context=None, batch=None, bytes_of=None, escalate=False):
         """landau_fp64: solve Landau matching in double for every cell (default: in float, in double
-        for cells above gamma_thr)."""
+        for cells above gamma_thr).  escalate: rerun numerical breakdowns of reduced-precision
+        simulations in double storage (see the module docstring)."""
         self.order = order
+        self.escalate = bool(escalate)
+        self.escalated = 0  # reruns in double storage
         self.landau_fp64 = bool(landau_fp64)
         self.budget = float(hbm_budget)
         self.chunk = int(chunk)
@@ -150,9 +158,11 @@ class Server:
     def _finish(self, req, status, detail="", m=None, admitted=None, steps=0):
         nz, ny, nx = req.shape
         empty = np.zeros(0)
+        if req.escalated_from:
+            detail = ("rerun in f64 after the %s run broke down" % req.escalated_from) + ("; " + detail if detail else "")
         self.results.append(Result(req.rid, m["n"] if m else empty, m["eps"] if m else empty, m["U"] if m else empty,
                                    m["totals"] if m else empty, admitted if admitted is not None else self.now(),
-                                   self.now(), req.arrival, nx * ny * nz, steps, status, detail))
+                                   self.now(), req.arrival, nx * ny * nz, steps, status, detail, req.storage))
 
     def cancel(self, rid):
         """Cancel request rid: a waiting one leaves the queue now, a running one at the end of the
@@ -244,6 +254,13 @@ class Server:
                 status, detail = "ok", ""
             except RLBError as e:  # a simulation that broke down (no Landau frame, NaN) is reported
                 m, status, detail = None, "failed", str(e)
+                if (self.escalate and e.status in (RLB_ENONCONV, RLB_ENAN) and req.storage != "f64"
+                        and req.rid not in self.cancelled):
+                    # rerun from the initial state in double storage, ahead of the waiting queue
+                    self._release(key)
+                    self.escalated += 1
+                    self.waiting.insert(0, dataclasses.replace(req, storage="f64", escalated_from=req.storage))
+                    continue
             self._release(key)
             self._finish(req, status, detail, m, t_adm, req.steps)
 
@@ -284,7 +301,8 @@ class Server:
                 "p99_tts_s": float(np.percentile(tts, 99)) if len(tts) else None,
                 "aggregate_mlups": upd / makespan / 1e6 if makespan > 0 else None,
                 "cell_updates": upd, "peak_hbm_gb": self.peak_in_use / 1e9, "peak_active": self.peak_active,
-                "queued_while_full": self.queued_while_full, "budget_gb": self.budget / 1e9}
+                "queued_while_full": self.queued_while_full, "budget_gb": self.budget / 1e9,
+                "escalated_to_f64": self.escalated}
 
     def close(self):
         for _, ctx, _, _ in self.active.values():

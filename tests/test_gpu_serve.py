@@ -1,4 +1,7 @@
-"""Serving: continuous batching under an HBM budget; every result equals its solo run."""
+"""Serving: continuous batching under an HBM budget; every result equals its solo run; a float
+simulation that breaks down is rerun in double storage."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -8,6 +11,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():  # pragma: no cover - CPU containers
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
+import oracle  # noqa: E402
 from paper_1301_3423_gb300 import RLB  # noqa: E402
 from paper_1301_3423_gb300 import serve  # noqa: E402
 
@@ -55,3 +59,26 @@ def test_realtime_stream_reports_latency_percentiles():
     assert st["requests"] == 10
     assert 0 < st["p50_tts_s"] <= st["p99_tts_s"]
     assert st["aggregate_mlups"] > 0
+
+
+def test_breakdown_in_float_is_rerun_in_double():
+    """Request 16 of the benchmark's serving stream, a 964-cell shock tube at eta/s = 0.01 in float
+    storage, loses Landau frames.  With escalation the server reruns it in double storage; the
+    double run loses them too (from step 490 the FP64 oracle finds cells without a Landau frame: the
+    model breaks down, not the precision), so the result is a failure that says it was rerun."""
+    req = dataclasses.replace(serve.poisson_requests(40, rate=20.0, seed=5, f16_fraction=0.3)[16], arrival=0.0)
+    assert (req.kind, req.shape, req.eta_over_s, req.storage) == ("tube", (964, 1, 1), 0.01, "f32")
+    lat = oracle.read_lattice(3)
+    o = oracle.OracleRLB(lat, req.shape[2], req.shape[1], req.shape[0], bc=req.bc, eta_over_s=req.eta_over_s)
+    o.init(*serve.initial_fields(req))
+    o.step(req.steps)
+    assert o.nonconv > 0  # the FP64 oracle's own step loses Landau frames
+    srv = serve.Server(hbm_budget=20e9, chunk=25, escalate=True)
+    try:
+        st = srv.run([req], realtime=False)
+    finally:
+        srv.close()
+    r = srv.results[0]
+    assert st["escalated_to_f64"] == 1
+    assert r.status == "failed" and r.storage == "f64"
+    assert "rerun in f64 after the f32 run broke down" in r.detail and "RLB_ENONCONV" in r.detail

@@ -1,12 +1,13 @@
 """Host-side logic of the continuous-batching server (serve.py) with fake simulations: admission
 against the budget, first-come-first-served waiting, rejection of requests above the budget,
 failures at creation (RLB_ENOMEM) reported as results, cancellation of waiting and running
-requests, and large lattices stepped on their own.  No GPU is involved."""
+requests, large lattices stepped on their own, and numerical breakdowns rerun in double storage.
+No GPU is involved."""
 import numpy as np
 import pytest
 
 from paper_1301_3423_gb300 import serve
-from paper_1301_3423_gb300.rlb import RLB_ENOMEM, RLBError
+from paper_1301_3423_gb300.rlb import RLB_ECUDA, RLB_ENOMEM, RLB_ENONCONV, RLBError
 
 
 class FakeCtx:
@@ -137,3 +138,43 @@ def test_large_lattices_step_on_their_own(monkeypatch):
     by = {r.rid: r for r in srv.results}
     assert np.all(by[0].n == 30) and np.all(by[1].n == 30)  # both took exactly 30 steps
     assert "f32" in srv.batches and len(srv.batches["f32"].members) == 0
+
+
+class BreakingCtx(FakeCtx):
+    """Request 1 loses Landau frames unless it runs in double storage; request 2 hits a device
+    error, which is not a numerical breakdown."""
+
+    def moments(self):
+        if self.req.rid == 1 and self.req.storage != "f64":
+            raise RLBError(RLB_ENONCONV, "12 cell updates without a Landau frame")
+        if self.req.rid == 2:
+            raise RLBError(RLB_ECUDA, "device error")
+        return super().moments()
+
+
+@pytest.mark.parametrize("escalate", [True, False])
+def test_numerical_breakdown_is_rerun_in_double_storage(monkeypatch, escalate):
+    monkeypatch.setattr(serve, "initial_fields", lambda r: (None, None, None))
+    log = []
+    created = []
+
+    def context(r):
+        created.append((r.rid, r.storage))
+        return BreakingCtx(r, log)
+
+    srv = serve.Server(hbm_budget=100.0, chunk=10, context=context, batch=lambda storage: FakeBatch(),
+                       bytes_of=lambda r: 20.0 if r.storage == "f64" else 10.0, escalate=escalate)
+    st = srv.run([req(0), req(1), req(2)], realtime=False)
+    r1 = [r for r in srv.results if r.rid == 1][0]
+    r2 = [r for r in srv.results if r.rid == 2][0]
+    assert r2.status == "failed" and "device error" in r2.detail  # never escalated
+    if escalate:
+        assert st["completed"] == 2 and st["failed"] == 1 and st["escalated_to_f64"] == 1
+        assert r1.status == "ok" and r1.storage == "f64" and r1.steps == 25
+        assert "rerun in f64 after the f32 run broke down" in r1.detail
+        assert created.count((1, "f32")) == 1 and created.count((1, "f64")) == 1
+        assert r1.arrival == 0.0 and r1.finished >= r1.admitted
+    else:
+        assert st["completed"] == 1 and st["failed"] == 2 and st["escalated_to_f64"] == 0
+        assert r1.status == "failed" and "Landau" in r1.detail and r1.storage == "f32"
+    assert srv.in_use == 0.0
