@@ -195,17 +195,18 @@ rlb_status rlb_autotune(rlb_ctx* ctx, int reps, int* variant, double ms[RLB_MAX_
  * fill the GPU together.  With a register variant (0..3) every member goes through the register
  * kernels (two launches: the members' interior rows in 32-cell segments, four per tile, then their
  * boundary cells).  With a pipelined variant (4 and up) the members whose rows start on 16-byte
- * boundaries and fill at least 7/8 of the tile lanes go through one launch of the batched
- * pipelined kernel over their row segments; with a row-tile variant (12 and up) the members with a
- * periodic x of at most 128 cells whose row tiles use at least 3/4 of the lanes and whose rows do
- * not fill segment tiles (any such member with half storage) go through a launch of the row-tile
- * kernel, and the other pipelined members through the row-segment
- * kernel of the same block layout; the others (e.g. 1 x 1 x N tubes) run through the register
- * kernels with the variant a context of that storage runs when it has no pipelined one (3 float,
- * 2 half, 0 double; see rlb_batch_member_variant).  Members keep their own buffers, parameters,
- * status and step counters; a member's populations after a batched run
- * are bitwise those of the same steps taken alone with the same step-kernel variant.  Members must
- * use the batch's stream.
+ * boundaries and fill enough of the tile lanes (7/8; 3/4 with one warp per float cell) go through
+ * one launch of the batched pipelined kernel over their row segments.  With a row-tile variant
+ * the members with a periodic x whose row tiles use at least 3/4 of the lanes go through a launch
+ * of the row-tile kernel (with two warps per float cell only those whose rows do not fill segment
+ * tiles), members that fill a 96-cell row tile better than a 128-cell one through a launch of the
+ * 96-cell row-tile kernel with the same warps (variant 19 beside 16), and the other pipelined
+ * members through the row-segment kernel of the same block layout.  The others (e.g. 1 x 1 x N
+ * tubes) run through the register kernels with the variant a context of that storage runs when it
+ * has no pipelined one (3 float, 2 half, 0 double; see rlb_batch_member_variant).  Members keep
+ * their own buffers, parameters, status and step counters; a member's populations after a batched
+ * run are bitwise those of the same steps taken alone with the same step-kernel variant.  Members
+ * must use the batch's stream.
  * ------------------------------------------------------------------------------------------- */
 typedef struct rlb_batch rlb_batch;
 
@@ -242,7 +243,8 @@ rlb_status rlb_batch_autotune(rlb_batch* b, int reps, int* variant, double ms[RL
 rlb_status rlb_batch_set_variant(rlb_batch* b, int variant);
 
 /* The step-kernel variant the batch runs the member in `slot` with, under the batch's current
- * variant: the batch's own; for a row-tile variant and a member that runs in row segments, the
+ * variant: the batch's own; the 96-cell row-tile variant for a member that runs in those beside a
+ * 128-cell row-tile variant; for a row-tile variant and a member that runs in row segments, the
  * row-segment variant of the same block layout; for a pipelined variant and a member whose rows do
  * not suit the tiles, the register fallback (3 float, 2 half, 0 double).  Running that member
  * alone with this variant gives the same populations bitwise.  -1 for an empty slot or NULL. */
